@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Benchmark of the LLG hot path: RK4 steps of a 256x256x16 film, FP32, one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
+
+One step = one classical RK4 step (four effective-field evaluations, each a
+forward x transform, the fused y/z transform + demag product, and the inverse
+x transform fused with exchange, anisotropy, Zeeman, LLG and the RK4 update),
+on synthetic inputs (seeded random unit vectors).  The L2 cache is flushed
+between timed steps (a 512 MiB write), so every step starts cold.
+
+Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) run one independent
+replica per rank: a single film does not shard without a global transpose.
+The reference arm (--impl reference) times the FP64 CPU oracle on the host.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LLG cell-steps/s at 256×256×16 (FP32 vs split-prec vs batched); adjoint/fwd time"
+UNIT = "cell-steps/s"
+FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--workload", default="film_256x256x16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-max-steps", type=int, default=8,
+                    help="reference arm: at most this many oracle RK4 steps are executed and timed")
+    return ap.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASON_NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={CLOCK_QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                p = [v.strip() for v in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(REASON_NAMES, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(grid):
+    """Compulsory HBM bytes per launch of each kernel class (FP32 RK4 stage).
+
+    x-forward: read m (12 B/cell), write the x-transformed field S
+    y/z:       read S, read the transformed kernel Kh, write S
+    x-inverse: read S, m_stage, m0; accumulator r/w (averaged over the 4
+               stages: 1.5 x 12 B/cell); write the next stage (12 B/cell)
+    """
+    nx, ny, nz = grid
+    N = nx * ny * nz
+    px = 1 if nx == 1 else 1 << (2 * nx - 2).bit_length()
+    py = 1 if ny == 1 else 1 << (2 * ny - 2).bit_length()
+    hx = 1 if px == 1 else px // 2 + 1
+    hy = 1 if py == 1 else py // 2 + 1
+    S = hx * 3 * nz * ny * 8
+    Kh = hx * 6 * nz * hy * 4
+    v = 12 * N
+    return {"xfwd": v + S, "yz": 2 * S + Kh, "xinv": S + v + v + 1.5 * v + v}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def stored_traffic(kernel):
+    """DRAM bytes per launch from a committed ncu capture, if the kernel source is unchanged since."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))[kernel]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_1501_07293_b300", "csrc", d.get("source", "field.cu"))
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return d["bytes_per_launch"] if sha == d.get("source_sha256") else None
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------
+def time_oracle(w, nsteps, warmup):
+    """Oracle RK4 steps on the full film; returns (cell-steps/s, cores used, seconds, steps)."""
+    from oracle import to_xyz
+    from oracle.llg import Film
+    from paper_1501_07293_b300 import inputs
+    mat = w.mat
+    film = Film(w.grid, w.delta, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma, b_ext=w.b_ext)
+    m = to_xyz(inputs.workload_state(w))
+    for _ in range(warmup):
+        m = film.rk4_step(m, w.dt)
+    c0, t0 = time.process_time(), time.perf_counter()
+    for _ in range(nsteps):
+        m = film.rk4_step(m, w.dt)
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    cores = max(1, int(round(cpu / wall)))
+    return w.ncells * nsteps / wall, cores, wall, nsteps
+
+
+def reference_arm(args, w):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    n = max(1, min(args.steps, args.ref_max_steps))
+    warm = min(args.warmup, 1)
+    val, cores, wall, n = time_oracle(w, n, warm)
+    sample = (f"{n} RK4 steps of the full {w.grid[0]}x{w.grid[1]}x{w.grid[2]} film (FP64 numpy oracle, "
+              f"{warm} warm-up step), of the {args.steps} requested")
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": n, "warmup": warm, "ms_per_step": 1e3 * wall / n, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "grid": list(w.grid), "integrator": "rk4", "dt_s": w.dt,
+                      "l2": "n/a (CPU)"},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# B300 arm
+# ---------------------------------------------------------------------------
+def b300_arm(args, w):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1501_07293_b300 import inputs
+    from paper_1501_07293_b300.solver import Solver
+
+    mat = w.mat
+    s = Solver(w.grid, w.delta, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma)
+    s.set_field(w.b_ext)
+    m0 = inputs.workload_state(w)
+    m0_dev = torch.from_numpy(m0).cuda()
+    s.set_m(m0_dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # warm-up (graph capture happens on the first step)
+    for _ in range(max(args.warmup, 0)):
+        flush.zero_()
+        s.step(1, w.dt)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed between steps (outside the events) ----
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    launches0 = s.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            s.step(1, w.dt)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    barrier()
+    launches = s.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(step_ms) / 1e3
+    t_max = max_over_ranks(t_dev)
+    value = world * w.ncells * K / t_max
+    s.sync()
+
+    # ---- per-kernel device times (event-bracketed eager replay of the same steps) ----
+    kt = np.zeros(3)
+    nk = min(K, 10)
+    for _ in range(nk):
+        flush.zero_()
+        torch.cuda.synchronize()
+        kt += s.step_timed(1, w.dt)
+    per_launch_ms = kt / (4 * nk)
+    names = ["xfwd", "yz", "xinv"]
+    kernels = {"xfwd": "k_xfwd", "yz": "k_yz", "xinv": "k_xinv"}
+    alg = algorithmic_bytes(w.grid)
+    dom = names[int(np.argmax(per_launch_ms))]
+    peak, peak_kind = measured_peaks()
+    achieved = alg[dom] / (per_launch_ms[names.index(dom)] * 1e-3) / 1e9
+    kernel_table = {n: {"ms_per_launch": float(per_launch_ms[i]), "alg_bytes": float(alg[n]),
+                        "GBps": float(alg[n] / (per_launch_ms[i] * 1e-3) / 1e9)} for i, n in enumerate(names)}
+
+    # ---- end to end through the C ABI with host buffers ----
+    m_host = torch.from_numpy(m0.copy()).pin_memory()
+    out_host = torch.empty_like(m_host).pin_memory()
+    Ke = min(K, 20)
+    eve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Ke)]
+    torch.cuda.synchronize()
+    for k in range(Ke):
+        flush.zero_()
+        eve[k][0].record(stream)
+        s.set_m(m_host)                # host -> device (pinned), normalise
+        s.step(1, w.dt)
+        s.get_m(out_host)              # device -> host (pinned)
+        eve[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(sum(a.elapsed_time(b) for a, b in eve) / 1e3)
+    e2e = world * w.ncells * Ke / t_e2e
+    nbytes = 3 * w.ncells * 4
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, cores, wall, n = time_oracle(w, 1, 0)
+        cpu = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} RK4 step of the full {w.grid[0]}x{w.grid[1]}x{w.grid[2]} film, "
+                         f"FP64 numpy oracle, {wall:.1f} s"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.grid), "delta_m": w.delta, "integrator": "rk4",
+                       "dt_s": w.dt, "variant": "fp32",
+                       "l2": "flushed between timed steps (512 MiB write outside the events)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "kernel": kernels[dom], "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": stored_traffic(kernels[dom])},
+            "kernels": kernel_table,
+            "step_fraction_of_hbm_roofline": (sum(alg[n] * 4 for n in names) * K / t_max / 1e9) / peak,
+            "wall_s_timed_region": t_wall,
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                    "path": "mm_set_m(pinned host) + mm_step(1) + mm_get_m(pinned host)"},
+            "gpu_launches": launches,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    from paper_1501_07293_b300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        reference_arm(args, w)
+    else:
+        b300_arm(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * mm_b300.h -- C ABI of the B300 finite-difference micromagnetic solver.
+ *
+ * The library advances the Landau-Lifshitz-Gilbert equation (eq. 2 of
+ * arXiv:1501.07293) on an nx x ny x nz grid of cubic cells of edge delta.
+ * The effective field (eq. 3) is the sum of
+ *   - exchange: six-neighbour Laplacian, eq. 4/5, with the Neumann rule of
+ *     eq. 6/7 (a missing neighbour is the cell itself);
+ *   - uniaxial anisotropy with the easy axis along x, eq. 8;
+ *   - demagnetising field: the discrete convolution of eq. 12/13 with the
+ *     tensor of eq. 10/11, evaluated through the convolution theorem, eq. 14,
+ *     on a zero-padded grid (Fig. 1);
+ *   - Zeeman field: a uniform mu0 H_ext plus an optional per-cell map.
+ *
+ * Conventions shared by every entry point
+ *   - SI units: delta in m, Ms in A/m, A in J/m, Ku in J/m^3, gamma in
+ *     rad/(s T), fields passed in as mu0 H (tesla), fields returned as H (A/m),
+ *     dt in s, energies in J.  mu0 = 4 pi 1e-7 exactly.
+ *   - The state is the unit vector m = M / Ms.  Every vector field is a
+ *     float32 array [3][nz][ny][nx] (component-major, x fastest); a scalar
+ *     map is float32 [nz][ny][nx].
+ *   - Array arguments named *_dev are device pointers; arguments documented
+ *     as "host or device" accept either kind (the copy direction is taken
+ *     from the pointer).  The caller owns every array it passes; the
+ *     context owns only its internal workspaces and copies what it keeps.
+ *   - Work is enqueued on the context's stream (mm_opts.stream) and is
+ *     asynchronous, except where an entry point says it synchronises.
+ *   - Every entry point returns an mm_status; none aborts or traps.  After a
+ *     failure mm_last_error() describes it.  A context is not thread-safe;
+ *     separate contexts are independent.
+ */
+#ifndef MM_B300_H
+#define MM_B300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mm_ctx mm_ctx;
+
+typedef enum {
+  MM_OK = 0,
+  MM_EINVAL = -1,        /* bad argument (null pointer, size, value)          */
+  MM_ENOMEM = -2,        /* device allocation failed                          */
+  MM_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed       */
+  MM_ETIMEOUT = -4,      /* a bounded device wait gave up                     */
+  MM_ENONFINITE = -5,    /* a NaN or Inf was found in the state or a result   */
+  MM_EUNSUPPORTED = -6   /* valid request this build does not implement       */
+} mm_status;
+
+enum { MM_FP32 = 0, MM_SPLIT_BF16 = 1, MM_SPLIT_FP16 = 2 };   /* mm_opts.precision */
+enum { MM_RK4 = 0, MM_EULER = 1 };                            /* mm_opts.integrator */
+
+/* Bit mask of effective-field terms (mm_heff). */
+enum {
+  MM_TERM_EXCHANGE = 1,
+  MM_TERM_ANISOTROPY = 2,
+  MM_TERM_DEMAG = 4,
+  MM_TERM_ZEEMAN = 8,
+  MM_TERM_ALL = 15
+};
+
+typedef struct {
+  int precision;    /* MM_FP32 (only value implemented)                                  */
+  int integrator;   /* MM_RK4 (classical, renormalise after the full step) or MM_EULER
+                       (the paper's explicit Euler step + renormalisation)               */
+  int self_term;    /* 1: keep the tensor's self offset K(0,0,0) = -I/3 (default);
+                       0: drop it as the paper's tensor listing does                    */
+  int obs_every;    /* reserved (0)                                                      */
+  void* stream;     /* cudaStream_t the context enqueues on; NULL = legacy default       */
+} mm_opts;
+
+/* Fill *opts with the defaults: MM_FP32, MM_RK4, self_term 1, obs_every 0, NULL stream. */
+void mm_default_opts(mm_opts* opts);
+
+/*
+ * Create a context for one film: grid = {nx, ny, nz} cells (each >= 1), cell
+ * edge delta, saturation magnetisation Ms, exchange constant A, anisotropy
+ * constant Ku (easy axis x), damping alpha and gyromagnetic ratio gamma.
+ * opts may be NULL (defaults).  Builds the demagnetising tensor (eq. 10/11)
+ * in FP64 on the device and transforms it once (eq. 14).  The initial state
+ * is m = (1, 0, 0) everywhere and the applied field is zero.  Synchronises.
+ * Returns MM_EUNSUPPORTED for grids whose padded transform does not fit the
+ * kernels of this build (see mm_padded_dims); *out is NULL on failure.
+ */
+int mm_create(mm_ctx** out, const int grid[3], double delta, double Ms, double A,
+              double Ku, double alpha, double gamma, const mm_opts* opts);
+
+/* Release the context and its device memory (NULL is accepted).  Synchronises. */
+void mm_destroy(mm_ctx* ctx);
+
+/* Change the stream subsequent calls enqueue on (a cudaStream_t; NULL = legacy default). */
+int mm_set_stream(mm_ctx* ctx, void* stream);
+
+/* Padded transform sizes {px, py, pz} chosen for the grid (px >= 2nx - 1, ...). */
+int mm_padded_dims(const mm_ctx* ctx, int padded[3]);
+
+/*
+ * Set the state from m (host or device, [3][nz][ny][nx] float32).  Each cell's
+ * vector is normalised on entry; a zero or non-finite vector gives
+ * MM_ENONFINITE when it is detected (at the next synchronising call).
+ */
+int mm_set_m(mm_ctx* ctx, const float* m);
+
+/* Copy the current state into m (host or device, [3][nz][ny][nx] float32). */
+int mm_get_m(mm_ctx* ctx, float* m);
+
+/*
+ * Applied field: b_ext = mu0 H_ext (tesla, 3 doubles, host).  h_map (host or
+ * device, [3][nz][ny][nx] tesla) is an optional per-cell addition, ku_map
+ * (host or device, [nz][ny][nx] J/m^3) an optional per-cell Ku that replaces
+ * the scalar Ku.  NULL clears a map.  The maps are copied.
+ */
+int mm_set_field(mm_ctx* ctx, const double b_ext[3], const float* h_map, const float* ku_map);
+
+/* Change the damping constant (the paper switches alpha between its relax and reverse phases). */
+int mm_set_alpha(mm_ctx* ctx, double alpha);
+
+/*
+ * Effective field (eq. 3) of the current state, restricted to the terms in
+ * term_mask (MM_TERM_*), written to H_dev ([3][nz][ny][nx] float32, A/m).
+ */
+int mm_heff(mm_ctx* ctx, float* H_dev, unsigned term_mask);
+
+/*
+ * Advance n >= 0 steps of size dt with the context's integrator.  One RK4
+ * step evaluates the effective field four times; the state is renormalised
+ * once after each full step (the paper renormalises after every Euler step).
+ * The step sequence is replayed from a captured CUDA graph.
+ */
+int mm_step(mm_ctx* ctx, int n, double dt);
+
+/*
+ * Energies of the current state (eq. 1 on the grid), in J:
+ * E[0] exchange, E[1] anisotropy, E[2] demagnetising, E[3] Zeeman, E[4] total.
+ * Accumulated in FP64.  Synchronises.
+ */
+int mm_energy(mm_ctx* ctx, double E[5]);
+
+/*
+ * Observables of the current state: out[0..2] = mean of m_x, m_y, m_z,
+ * out[3] = max over cells of |dm/dt| (rad/s), out[4] = steps taken since the
+ * last mm_set_m.  Accumulated in FP64.  Synchronises.  Returns MM_ENONFINITE
+ * if the state holds a NaN or Inf.
+ */
+int mm_observables(mm_ctx* ctx, double out[5]);
+
+/*
+ * Profiling variant of mm_step: advance n steps launching every kernel
+ * eagerly (no graph) with CUDA events around each launch, and add the device
+ * time of each kernel class to ms_out[3]: [0] x-forward transforms, [1] y/z
+ * transforms with the demag product, [2] x-inverse transforms with the
+ * field/LLG update.  ms_out is host memory, accumulated into (not cleared).
+ * Same numerical result as mm_step.  Synchronises after every step.
+ */
+int mm_step_timed(mm_ctx* ctx, int n, double dt, double ms_out[3]);
+
+/* Number of kernels this context has enqueued so far (graph nodes counted per replay). */
+long long mm_launch_count(const mm_ctx* ctx);
+
+/* Block until the context's stream is idle; reports a pending device-side error. */
+int mm_sync(mm_ctx* ctx);
+
+/* Text of the last failure of this context ("" if none); ctx NULL gives the last create failure. */
+const char* mm_last_error(const mm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MM_B300_H */

@@ -15,7 +15,7 @@ Two routes that must agree:
 """
 import numpy as np
 
-from .tensor import COMPONENTS
+from .tensor import COMPONENTS, tensor_at
 
 _PAIRS = {(0, 0): "xx", (1, 1): "yy", (2, 2): "zz",
           (0, 1): "xy", (1, 0): "xy", (0, 2): "xz", (2, 0): "xz",
@@ -40,6 +40,28 @@ def demag_direct(m, Ms, K):
                         tot += np.sum(M[b] * K[_PAIRS[(a, b)]][sl])
                     H[a, i, j, k] = tot
     return H
+
+
+def demag_at_cells(m, Ms, cells, self_term=True):
+    """Eq. 13 by brute force at a few target cells only (for grids too large for demag_direct).
+
+    The tensor is evaluated (eq. 10/11) at exactly the offsets l - i the sum
+    needs.  Returns an array (len(cells), 3).
+    """
+    _, nx, ny, nz = m.shape
+    M = Ms * np.asarray(m, dtype=np.float64)
+    L = np.arange(nx)[:, None, None]
+    Mm = np.arange(ny)[None, :, None]
+    Nn = np.arange(nz)[None, None, :]
+    out = np.zeros((len(cells), 3))
+    for q, (i, j, k) in enumerate(cells):
+        K = tensor_at(L - i, Mm - j, Nn - k)
+        if not self_term:
+            for c in COMPONENTS:
+                K[c][i, j, k] = 0.0
+        for a in range(3):
+            out[q, a] = sum(np.sum(M[b] * K[_PAIRS[(a, b)]]) for b in range(3))
+    return out
 
 
 class FFTDemag:

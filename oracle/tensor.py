@@ -29,16 +29,15 @@ import numpy as np
 COMPONENTS = ("xx", "yy", "zz", "xy", "xz", "yz")
 
 
-def demag_tensor(nx, ny, nz, delta=1.0, self_term=True):
-    """K_ab(I, J, K) for all |I| < nx, |J| < ny, |K| < nz.
+def tensor_at(I, J, Kk, delta=1.0):
+    """Eq. 10/11 at offsets (I, J, K) given as broadcastable arrays of integers.
 
-    Returns a dict component -> float64 array of shape (2nx-1, 2ny-1, 2nz-1)
-    indexed [I + nx - 1, J + ny - 1, K + nz - 1].
+    Returns a dict component -> float64 array of the broadcast shape.
     """
-    I = np.arange(-nx + 1, nx, dtype=np.float64)[:, None, None]
-    J = np.arange(-ny + 1, ny, dtype=np.float64)[None, :, None]
-    Kk = np.arange(-nz + 1, nz, dtype=np.float64)[None, None, :]
-    shape = (2 * nx - 1, 2 * ny - 1, 2 * nz - 1)
+    I = np.asarray(I, dtype=np.float64)
+    J = np.asarray(J, dtype=np.float64)
+    Kk = np.asarray(Kk, dtype=np.float64)
+    shape = np.broadcast_shapes(I.shape, J.shape, Kk.shape)
     acc = {c: np.zeros(shape) for c in COMPONENTS}
     for i in (0, 1):
         for j in (0, 1):
@@ -55,10 +54,22 @@ def demag_tensor(nx, ny, nz, delta=1.0, self_term=True):
                 acc["xz"] += s * np.log(y + r)
                 acc["yz"] += s * np.log(x + r)
     pref = 1.0 / (4.0 * np.pi)
-    out = {
+    return {
         "xx": pref * acc["xx"], "yy": pref * acc["yy"], "zz": pref * acc["zz"],
         "xy": -pref * acc["xy"], "xz": -pref * acc["xz"], "yz": -pref * acc["yz"],
     }
+
+
+def demag_tensor(nx, ny, nz, delta=1.0, self_term=True):
+    """K_ab(I, J, K) for all |I| < nx, |J| < ny, |K| < nz.
+
+    Returns a dict component -> float64 array of shape (2nx-1, 2ny-1, 2nz-1)
+    indexed [I + nx - 1, J + ny - 1, K + nz - 1].
+    """
+    I = np.arange(-nx + 1, nx)[:, None, None]
+    J = np.arange(-ny + 1, ny)[None, :, None]
+    Kk = np.arange(-nz + 1, nz)[None, None, :]
+    out = tensor_at(I, J, Kk, delta)
     if not self_term:
         for c in COMPONENTS:
             out[c][nx - 1, ny - 1, nz - 1] = 0.0

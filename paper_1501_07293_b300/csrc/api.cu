@@ -1,0 +1,466 @@
+// C ABI of libmm_b300 (declared in include/mm_b300.h): context life cycle,
+// state and field set-up, the captured step graph, energies and observables.
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "common.cuh"
+
+static char g_create_err[512] = "";
+
+int mm_fail(mm_ctx* c, int code, const char* fmt, ...) {
+  char* dst = c ? c->err : g_create_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+static int pow2_at_least(int v) {
+  int p = 1;
+  while (p < v) p *= 2;
+  return p;
+}
+
+static Phys make_phys(const mm_ctx* c) {
+  Phys ph;
+  const double Ms = c->Ms, dl = c->delta;
+  ph.c_ex = (float)(2.0 * c->A / (Ms * dl * dl));
+  ph.c_an = (float)(2.0 * c->Ku / Ms);
+  ph.c_an_map = (float)(2.0 / Ms);
+  ph.c_d = (float)(MM_MU0 * Ms / ((double)c->d.px * (double)c->d.py));
+  ph.bx = (float)c->b_ext[0];
+  ph.by = (float)c->b_ext[1];
+  ph.bz = (float)c->b_ext[2];
+  const double g = c->gamma / (1.0 + c->alpha * c->alpha);
+  ph.g1 = (float)(-g);
+  ph.g2 = (float)(-c->alpha * g);
+  ph.inv_mu0 = (float)(1.0 / MM_MU0);
+  return ph;
+}
+
+static void drop_graphs(mm_ctx* c) {
+  for (int i = 0; i < 2; ++i)
+    if (c->graph[i]) {
+      cudaGraphExecDestroy(c->graph[i]);
+      c->graph[i] = nullptr;
+    }
+  c->graph_valid = 0;
+}
+
+extern "C" void mm_default_opts(mm_opts* o) {
+  if (!o) return;
+  o->precision = MM_FP32;
+  o->integrator = MM_RK4;
+  o->self_term = 1;
+  o->obs_every = 0;
+  o->stream = nullptr;
+}
+
+static void free_ctx(mm_ctx* c) {
+  if (!c) return;
+  drop_graphs(c);
+  cudaFree(c->m0); cudaFree(c->stA); cudaFree(c->stB); cudaFree(c->acc); cudaFree(c->Hs);
+  cudaFree(c->hmap); cudaFree(c->kumap); cudaFree(c->S); cudaFree(c->Kh); cudaFree(c->tw);
+  cudaFree(c->red); cudaFree(c->red_out); cudaFree(c->dflag);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->ev) cudaEventDestroy(c->ev);
+  free(c);
+}
+
+extern "C" void mm_destroy(mm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+#define ALLOC(ptr, bytes)                                                                       \
+  do {                                                                                          \
+    if (cudaMalloc((void**)&(ptr), (bytes)) != cudaSuccess) {                                   \
+      cudaGetLastError();                                                                       \
+      rc = mm_fail(nullptr, MM_ENOMEM, "cannot allocate %zu bytes of device memory", (size_t)(bytes)); \
+      goto fail;                                                                                \
+    }                                                                                           \
+  } while (0)
+
+extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double Ms, double A, double Ku,
+                         double alpha, double gamma, const mm_opts* opts) {
+  if (!out) return mm_fail(nullptr, MM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!grid) return mm_fail(nullptr, MM_EINVAL, "grid is NULL");
+  if (grid[0] < 1 || grid[1] < 1 || grid[2] < 1)
+    return mm_fail(nullptr, MM_EINVAL, "grid %d x %d x %d: every size must be >= 1", grid[0], grid[1], grid[2]);
+  if (!(delta > 0) || !(Ms > 0) || !(A >= 0) || !(Ku >= 0 || Ku < 0) || !(alpha >= 0) || !(gamma > 0))
+    return mm_fail(nullptr, MM_EINVAL, "material parameters out of range (delta, Ms, gamma > 0; A, alpha >= 0)");
+  mm_opts o;
+  mm_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.precision != MM_FP32)
+    return mm_fail(nullptr, MM_EUNSUPPORTED, "precision mode %d is not implemented (MM_FP32 only)", o.precision);
+  if (o.integrator != MM_RK4 && o.integrator != MM_EULER)
+    return mm_fail(nullptr, MM_EINVAL, "unknown integrator %d", o.integrator);
+
+  int rc = MM_OK;
+  mm_ctx* c = (mm_ctx*)calloc(1, sizeof(mm_ctx));
+  if (!c) return mm_fail(nullptr, MM_ENOMEM, "host allocation failed");
+  c->d.nx = grid[0]; c->d.ny = grid[1]; c->d.nz = grid[2];
+  c->d.px = grid[0] == 1 ? 1 : pow2_at_least(2 * grid[0] - 1);
+  c->d.py = grid[1] == 1 ? 1 : pow2_at_least(2 * grid[1] - 1);
+  c->d.hx = c->d.px == 1 ? 1 : c->d.px / 2 + 1;
+  c->d.hy = c->d.py == 1 ? 1 : c->d.py / 2 + 1;
+  c->d.N = (long long)grid[0] * grid[1] * grid[2];
+  c->delta = delta; c->Ms = Ms; c->A = A; c->Ku = Ku; c->alpha = alpha; c->gamma = gamma;
+  c->opts = o;
+  c->stream = (cudaStream_t)o.stream;
+  c->Lmax = c->d.px > c->d.py ? c->d.px : c->d.py;
+  if (c->Lmax < 2) c->Lmax = 2;
+  {
+    char why[256];
+    if (!mm_supported(c->d, why, sizeof why)) {
+      rc = mm_fail(nullptr, MM_EUNSUPPORTED, "grid %d x %d x %d: %s", grid[0], grid[1], grid[2], why);
+      goto fail;
+    }
+  }
+  {
+    const size_t v3 = sizeof(float) * 3 * (size_t)c->d.N;
+    ALLOC(c->m0, v3);
+    ALLOC(c->stA, v3);
+    ALLOC(c->stB, v3);
+    ALLOC(c->acc, v3);
+    ALLOC(c->Hs, v3);
+    ALLOC(c->S, sizeof(float2) * (size_t)c->d.hx * 3 * c->d.nz * c->d.ny);
+    ALLOC(c->Kh, sizeof(float) * (size_t)c->d.hx * 6 * c->d.nz * c->d.hy);
+    ALLOC(c->tw, sizeof(float2) * 2 * (size_t)c->Lmax);
+    long long nb = (c->d.N + 255) / 256;
+    if (nb > 1184) nb = 1184;
+    if (nb < 1) nb = 1;
+    c->red_blocks = (int)nb;
+    ALLOC(c->red, sizeof(double) * 9 * (size_t)nb);
+    ALLOC(c->red_out, sizeof(double) * 16);
+    ALLOC(c->dflag, sizeof(int) * 4);
+  }
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    rc = mm_fail(nullptr, MM_ECUDA, "stream/event creation failed");
+    goto fail;
+  }
+  if (cudaMemsetAsync(c->dflag, 0, sizeof(int) * 4, c->stream) != cudaSuccess) {
+    rc = mm_fail(nullptr, MM_ECUDA, "memset failed");
+    goto fail;
+  }
+  rc = mm_build_kernel(c);
+  if (rc != MM_OK) {
+    snprintf(g_create_err, sizeof g_create_err, "%s", c->err);
+    goto fail;
+  }
+  {
+    // m = (1, 0, 0)
+    float* h = (float*)calloc(3 * (size_t)c->d.N, sizeof(float));
+    if (!h) { rc = mm_fail(nullptr, MM_ENOMEM, "host allocation failed"); goto fail; }
+    for (long long i = 0; i < c->d.N; ++i) h[i] = 1.0f;
+    cudaError_t e = cudaMemcpy(c->m0, h, sizeof(float) * 3 * (size_t)c->d.N, cudaMemcpyHostToDevice);
+    free(h);
+    if (e != cudaSuccess) { rc = mm_fail(nullptr, MM_ECUDA, "initial state upload failed"); goto fail; }
+  }
+  *out = c;
+  return MM_OK;
+fail:
+  free_ctx(c);
+  return rc;
+}
+
+extern "C" int mm_set_stream(mm_ctx* c, void* stream) {
+  if (!c) return MM_EINVAL;
+  c->stream = (cudaStream_t)stream;
+  c->opts.stream = stream;
+  return MM_OK;
+}
+
+extern "C" int mm_padded_dims(const mm_ctx* c, int padded[3]) {
+  if (!c || !padded) return MM_EINVAL;
+  padded[0] = c->d.px;
+  padded[1] = c->d.py;
+  padded[2] = c->d.nz;  // z is summed directly, never padded
+  return MM_OK;
+}
+
+static float* state_ptr(mm_ctx* c) { return c->cur ? c->stA : c->m0; }
+
+extern "C" int mm_set_m(mm_ctx* c, const float* m) {
+  if (!c) return MM_EINVAL;
+  if (!m) return mm_fail(c, MM_EINVAL, "mm_set_m: m is NULL");
+  c->cur = 0;
+  MM_CK(c, cudaMemcpyAsync(c->m0, m, sizeof(float) * 3 * (size_t)c->d.N, cudaMemcpyDefault, c->stream));
+  if (launch_normalise(c->d, c->m0, c->dflag, c->stream) < 0) return mm_fail(c, MM_ECUDA, "normalise launch failed");
+  c->launches++;
+  c->steps = 0;
+  return MM_OK;
+}
+
+extern "C" int mm_get_m(mm_ctx* c, float* m) {
+  if (!c) return MM_EINVAL;
+  if (!m) return mm_fail(c, MM_EINVAL, "mm_get_m: m is NULL");
+  MM_CK(c, cudaMemcpyAsync(m, state_ptr(c), sizeof(float) * 3 * (size_t)c->d.N, cudaMemcpyDefault, c->stream));
+  return MM_OK;
+}
+
+extern "C" int mm_set_field(mm_ctx* c, const double b_ext[3], const float* h_map, const float* ku_map) {
+  if (!c) return MM_EINVAL;
+  if (!b_ext) return mm_fail(c, MM_EINVAL, "mm_set_field: b_ext is NULL");
+  for (int i = 0; i < 3; ++i) c->b_ext[i] = b_ext[i];
+  const size_t N = (size_t)c->d.N;
+  if (h_map) {
+    if (!c->hmap && cudaMalloc(&c->hmap, sizeof(float) * 3 * N) != cudaSuccess) {
+      cudaGetLastError();
+      return mm_fail(c, MM_ENOMEM, "cannot allocate the field map");
+    }
+    MM_CK(c, cudaMemcpyAsync(c->hmap, h_map, sizeof(float) * 3 * N, cudaMemcpyDefault, c->stream));
+  } else if (c->hmap) {
+    MM_CK(c, cudaStreamSynchronize(c->stream));
+    cudaFree(c->hmap);
+    c->hmap = nullptr;
+  }
+  if (ku_map) {
+    if (!c->kumap && cudaMalloc(&c->kumap, sizeof(float) * N) != cudaSuccess) {
+      cudaGetLastError();
+      return mm_fail(c, MM_ENOMEM, "cannot allocate the Ku map");
+    }
+    MM_CK(c, cudaMemcpyAsync(c->kumap, ku_map, sizeof(float) * N, cudaMemcpyDefault, c->stream));
+  } else if (c->kumap) {
+    MM_CK(c, cudaStreamSynchronize(c->stream));
+    cudaFree(c->kumap);
+    c->kumap = nullptr;
+  }
+  drop_graphs(c);  // kernel arguments changed
+  return MM_OK;
+}
+
+extern "C" int mm_set_alpha(mm_ctx* c, double alpha) {
+  if (!c) return MM_EINVAL;
+  if (!(alpha >= 0)) return mm_fail(c, MM_EINVAL, "alpha must be >= 0");
+  c->alpha = alpha;
+  drop_graphs(c);
+  return MM_OK;
+}
+
+static StageArgs base_args(mm_ctx* c) {
+  StageArgs a;
+  memset(&a, 0, sizeof a);
+  a.hmap = c->hmap;
+  a.kumap = c->kumap;
+  return a;
+}
+
+extern "C" int mm_heff(mm_ctx* c, float* H, unsigned mask) {
+  if (!c) return MM_EINVAL;
+  if (!H) return mm_fail(c, MM_EINVAL, "mm_heff: H is NULL");
+  if (mask & ~(unsigned)MM_TERM_ALL) return mm_fail(c, MM_EINVAL, "mm_heff: bad term mask 0x%x", mask);
+  StageArgs a = base_args(c);
+  a.m_in = state_ptr(c);
+  a.H_out = H;
+  a.mode = 0;
+  a.mask = mask;
+  const int k = launch_field_eval(c->d, make_phys(c), a, c->tw, c->S, c->Kh, c->stream);
+  if (k < 0) return mm_fail(c, MM_ECUDA, "field kernels failed to launch (%d): %s", k, cudaGetErrorString(cudaGetLastError()));
+  c->launches += k;
+  return MM_OK;
+}
+
+// Enqueue one step on stream s; `from` = buffer holding the state (Euler alternates).
+static int enqueue_step(mm_ctx* c, cudaStream_t s, double dt, int from, long long* nk) {
+  const Phys ph = make_phys(c);
+  StageArgs a = base_args(c);
+  a.dt = (float)dt;
+  *nk = 0;
+  if (c->opts.integrator == MM_EULER) {
+    a.mode = 2;
+    a.m_in = from ? c->stA : c->m0;
+    a.m_out = from ? c->m0 : c->stA;
+    const int k = launch_field_eval(c->d, ph, a, c->tw, c->S, c->Kh, s);
+    if (k < 0) return k;
+    *nk += k;
+    return 0;
+  }
+  a.mode = 1;
+  a.m0 = c->m0;
+  a.acc = c->acc;
+  const float* in[4] = {c->m0, c->stA, c->stB, c->stA};
+  float* outp[4] = {c->stA, c->stB, c->stA, c->m0};
+  for (int s4 = 0; s4 < 4; ++s4) {
+    a.stage = s4;
+    a.m_in = in[s4];
+    a.m_out = outp[s4];
+    const int k = launch_field_eval(c->d, ph, a, c->tw, c->S, c->Kh, s);
+    if (k < 0) return k;
+    *nk += k;
+  }
+  return 0;
+}
+
+static int build_graphs(mm_ctx* c, double dt) {
+  drop_graphs(c);
+  const int ng = c->opts.integrator == MM_EULER ? 2 : 1;
+  for (int g = 0; g < ng; ++g) {
+    cudaGraph_t graph;
+    MM_CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    long long nk = 0;
+    const int r = enqueue_step(c, c->cap_stream, dt, g, &nk);
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (r < 0 || e != cudaSuccess) {
+      cudaGetLastError();
+      return mm_fail(c, MM_ECUDA, "graph capture failed (%d, %s)", r, cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&c->graph[g], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return mm_fail(c, MM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    c->graph_nodes[g] = nk;
+  }
+  c->graph_valid = 1;
+  c->graph_dt = dt;
+  c->graph_integrator = c->opts.integrator;
+  return MM_OK;
+}
+
+extern "C" int mm_step(mm_ctx* c, int n, double dt) {
+  if (!c) return MM_EINVAL;
+  if (n < 0) return mm_fail(c, MM_EINVAL, "mm_step: n = %d < 0", n);
+  if (!(dt > 0) || dt > 1e-6) return mm_fail(c, MM_EINVAL, "mm_step: dt = %g s out of range (0, 1e-6]", dt);
+  if (n == 0) return MM_OK;
+  if (!c->graph_valid || c->graph_dt != dt || c->graph_integrator != c->opts.integrator) {
+    const int r = build_graphs(c, dt);
+    if (r != MM_OK) return r;
+  }
+  for (int i = 0; i < n; ++i) {
+    const int g = c->opts.integrator == MM_EULER ? c->cur : 0;
+    MM_CK(c, cudaGraphLaunch(c->graph[g], c->stream));
+    c->launches += c->graph_nodes[g];
+    if (c->opts.integrator == MM_EULER) c->cur ^= 1;
+  }
+  c->steps += n;
+  return MM_OK;
+}
+
+extern "C" int mm_step_timed(mm_ctx* c, int n, double dt, double ms_out[3]) {
+  if (!c) return MM_EINVAL;
+  if (!ms_out) return mm_fail(c, MM_EINVAL, "mm_step_timed: ms_out is NULL");
+  if (n < 0) return mm_fail(c, MM_EINVAL, "mm_step_timed: n = %d < 0", n);
+  if (!(dt > 0) || dt > 1e-6) return mm_fail(c, MM_EINVAL, "mm_step_timed: dt = %g s out of range", dt);
+  const Phys ph = make_phys(c);
+  cudaEvent_t ev[13];
+  for (int i = 0; i < 13; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+      for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+      return mm_fail(c, MM_ECUDA, "event creation failed");
+    }
+  int rc = MM_OK;
+  for (int step = 0; step < n && rc == MM_OK; ++step) {
+    StageArgs a = base_args(c);
+    a.dt = (float)dt;
+    int nst = 4;
+    const float* in[4] = {c->m0, c->stA, c->stB, c->stA};
+    float* outp[4] = {c->stA, c->stB, c->stA, c->m0};
+    if (c->opts.integrator == MM_EULER) {
+      nst = 1;
+      a.mode = 2;
+      in[0] = c->cur ? c->stA : c->m0;
+      outp[0] = c->cur ? c->m0 : c->stA;
+    } else {
+      a.mode = 1;
+      a.m0 = c->m0;
+      a.acc = c->acc;
+    }
+    int ne = 0;
+    cudaEventRecord(ev[ne++], c->stream);
+    for (int s4 = 0; s4 < nst && rc == MM_OK; ++s4) {
+      a.stage = s4;
+      a.m_in = in[s4];
+      a.m_out = outp[s4];
+      for (int part = 0; part < 3; ++part) {
+        if (launch_field_part(c->d, ph, a, c->tw, c->S, c->Kh, c->stream, part) < 0) {
+          rc = mm_fail(c, MM_ECUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+          break;
+        }
+        c->launches++;
+        cudaEventRecord(ev[ne++], c->stream);
+      }
+    }
+    if (rc != MM_OK) break;
+    if (cudaEventSynchronize(ev[ne - 1]) != cudaSuccess) {
+      rc = mm_fail(c, MM_ECUDA, "step failed: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    for (int k = 1; k < ne; ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[k - 1], ev[k]);
+      ms_out[(k - 1) % 3] += ms;
+    }
+    if (c->opts.integrator == MM_EULER) c->cur ^= 1;
+    c->steps++;
+  }
+  for (int i = 0; i < 13; ++i) cudaEventDestroy(ev[i]);
+  return rc;
+}
+
+static int check_flag(mm_ctx* c) {
+  int h[4];
+  MM_CK(c, cudaMemcpyAsync(h, c->dflag, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  MM_CK(c, cudaStreamSynchronize(c->stream));
+  if (h[0]) {
+    cudaMemsetAsync(c->dflag, 0, sizeof(int) * 4, c->stream);
+    return mm_fail(c, MM_ENONFINITE, "non-finite or zero magnetisation vector found");
+  }
+  return MM_OK;
+}
+
+static int run_reduce(mm_ctx* c, double* host) {
+  StageArgs a = base_args(c);
+  a.m_in = state_ptr(c);
+  a.H_out = c->Hs;
+  a.mode = 0;
+  a.mask = MM_TERM_DEMAG;
+  const Phys ph = make_phys(c);
+  int k = launch_field_eval(c->d, ph, a, c->tw, c->S, c->Kh, c->stream);
+  if (k < 0) return mm_fail(c, MM_ECUDA, "field kernels failed to launch");
+  c->launches += k;
+  k = launch_reduce(c->d, ph, state_ptr(c), c->Hs, c->hmap, c->kumap, c->A, c->Ku, c->delta, c->Ms, c->red,
+                    c->red_blocks, c->red_out, c->dflag, c->stream);
+  if (k < 0) return mm_fail(c, MM_ECUDA, "reduction kernels failed to launch");
+  c->launches += k;
+  MM_CK(c, cudaMemcpyAsync(host, c->red_out, sizeof(double) * 9, cudaMemcpyDeviceToHost, c->stream));
+  return check_flag(c);
+}
+
+extern "C" int mm_energy(mm_ctx* c, double E[5]) {
+  if (!c) return MM_EINVAL;
+  if (!E) return mm_fail(c, MM_EINVAL, "mm_energy: E is NULL");
+  double r[9];
+  const int rc = run_reduce(c, r);
+  if (rc != MM_OK) return rc;
+  E[0] = r[0]; E[1] = r[1]; E[2] = r[2]; E[3] = r[3];
+  E[4] = r[0] + r[1] + r[2] + r[3];
+  return MM_OK;
+}
+
+extern "C" int mm_observables(mm_ctx* c, double out[5]) {
+  if (!c) return MM_EINVAL;
+  if (!out) return mm_fail(c, MM_EINVAL, "mm_observables: out is NULL");
+  double r[9];
+  const int rc = run_reduce(c, r);
+  if (rc != MM_OK) return rc;
+  out[0] = r[4]; out[1] = r[5]; out[2] = r[6]; out[3] = r[7];
+  out[4] = (double)c->steps;
+  return MM_OK;
+}
+
+extern "C" long long mm_launch_count(const mm_ctx* c) { return c ? c->launches : -1; }
+
+extern "C" int mm_sync(mm_ctx* c) {
+  if (!c) return MM_EINVAL;
+  MM_CK(c, cudaStreamSynchronize(c->stream));
+  return check_flag(c);
+}
+
+extern "C" const char* mm_last_error(const mm_ctx* c) { return c ? c->err : g_create_err; }

@@ -1,0 +1,112 @@
+// Internal declarations shared by the CUDA translation units of libmm_b300.
+//
+// Data layout in HBM (all float32 unless noted):
+//   m0, stA, stB, acc, Hs   [3][nz][ny][nx]   unit-vector state, RK4 stage
+//                                             buffers, RK4 accumulator, scratch
+//   S                       [hx][3][nz][ny]   float2: x-transformed field
+//                                             (kx-major, so one kx column of the
+//                                             y/z pass is a contiguous slab)
+//   Kh                      [hx][6][nz][hy]   demag kernel transformed along x
+//                                             and y, real space along z
+//                                             (pairs xx yy zz xy xz yz)
+//   tw                      [2 Lmax]          float2 twiddles; the table of
+//                                             length L sits at offset L
+//   hx = px/2 + 1, hy = py/2 + 1 (1 when the padded size is 1).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mm_b300.h"
+
+#define MM_PI 3.14159265358979323846
+#define MM_MU0 (4.0e-7 * MM_PI)
+
+// Grid and launch geometry of one film, passed by value to kernels.
+struct Dims {
+  int nx, ny, nz;
+  int px, py;
+  int hx, hy;
+  long long N;  // nx*ny*nz
+};
+
+// Per-cell physics constants, float32, precomputed in double on the host.
+struct Phys {
+  float c_ex;      // 2A/(Ms delta^2): B_exch = c_ex * sum_nb (m_nb - m)      [T]
+  float c_an;      // 2Ku/Ms: B_anis,x = c_an * m_x (scalar Ku)               [T]
+  float c_an_map;  // 2/Ms: B_anis,x = c_an_map * Ku(cell) * m_x (Ku map)     [T m^3/J]
+  float c_d;       // mu0 Ms/(px py): B_demag = c_d * (inverse transform)     [T]
+  float bx, by, bz;  // uniform mu0 H_ext                                      [T]
+  float g1, g2;    // -gamma/(1+a^2), -alpha gamma/(1+a^2)
+  float inv_mu0;   // 1/mu0 (tesla -> A/m)
+};
+
+// One field evaluation / stage.  mode: 0 = write H_eff, 1 = RK4 stage, 2 = Euler step.
+struct StageArgs {
+  const float* m_in;   // state the field is evaluated at (read with neighbours)
+  const float* m0;     // RK4 base state
+  float* acc;          // RK4 accumulator sum_s w_s k_s
+  float* m_out;        // next stage state / new state
+  float* H_out;        // mode 0 output (A/m)
+  const float* hmap;   // per-cell applied field (T) or null
+  const float* kumap;  // per-cell Ku (J/m^3) or null
+  int mode;
+  int stage;           // RK4 stage 0..3
+  unsigned mask;       // mode 0: MM_TERM_* terms to write
+  float dt;
+};
+
+struct mm_ctx {
+  Dims d;
+  double delta, Ms, A, Ku, alpha, gamma;
+  double b_ext[3];
+  mm_opts opts;
+  cudaStream_t stream;       // caller's stream (may be the legacy default stream)
+  cudaStream_t cap_stream;   // private stream used only for graph capture
+  cudaEvent_t ev;            // orders capture/work between the two streams
+  float *m0, *stA, *stB, *acc, *Hs, *hmap, *kumap;
+  float2* S;
+  float* Kh;
+  float2* tw;
+  int Lmax;
+  double* red;               // reduction partials
+  double* red_out;           // final reduction result (device)
+  int red_blocks;
+  int* dflag;                // device error flags: [0] non-finite state
+  int cur;                   // Euler: 0 -> state in m0, 1 -> state in stA
+  cudaGraphExec_t graph[2];  // RK4: graph[0]; Euler: graph[0] (m0->stA), graph[1] (stA->m0)
+  int graph_valid;
+  double graph_dt;
+  int graph_integrator;
+  long long graph_nodes[2];
+  long long launches;
+  long long steps;
+  char err[512];
+};
+
+// Status helpers (api.cu)
+int mm_fail(mm_ctx* c, int code, const char* fmt, ...);
+#define MM_CK(ctx, call)                                                              \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return mm_fail((ctx), MM_ECUDA, "%s failed: %s (%s:%d)", #call,                 \
+                     cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+  } while (0)
+
+// setup.cu: build Kh (FP64 tensor, FP64 2D transform, FP32 store) and the twiddles.
+int mm_build_kernel(mm_ctx* c);
+
+// field.cu: launchers (return number of kernels launched, or <0 on launch error)
+int mm_supported(const Dims& d, char* why, int nwhy);
+int launch_field_eval(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw,
+                      float2* S, const float* Kh, cudaStream_t s);
+// part: 0 = x-forward, 1 = y/z + product, 2 = x-inverse + update (one launch each)
+int launch_field_part(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
+                      const float* Kh, cudaStream_t s, int part);
+int launch_normalise(const Dims& d, float* m, int* flag, cudaStream_t s);
+
+// reduce.cu
+int launch_reduce(const Dims& d, const Phys& ph, const float* m, const float* Hd,
+                  const float* hmap, const float* kumap, double A, double Ku, double delta,
+                  double Ms, double* partials, int nblocks, double* out, int* flag,
+                  cudaStream_t s);

@@ -1,0 +1,146 @@
+// FP32 FFT building blocks for the demagnetising convolution (eq. 14).
+//
+// A "team" of T lanes (T a power of two, T <= 32, all in one warp) transforms
+// one power-of-two row of length L held in shared memory, in place, with the
+// Stockham auto-sort formulation: pass by pass every lane loads R values at
+// stride L/R into registers, applies the twiddles of the pass, does a radix-R
+// DFT in registers and stores the R results at their auto-sorted places.
+// Radices 8, then 4 or 2 for the remainder.  Results are in natural order.
+// DIR = -1 is the forward transform exp(-2 pi i nk/L), DIR = +1 the
+// unnormalised inverse.  Twiddles come from a table tw[m] = exp(-2 pi i m/LT)
+// of length LT = L * TWS (TWS a power-of-two stride), so one table serves a
+// transform and its half-length sub-transforms.
+#pragma once
+#include <cuda_runtime.h>
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by i
+__device__ __forceinline__ float2 cmuli(float2 a) { return make_float2(-a.y, a.x); }
+// multiply by the quarter-turn of direction DIR: -i (forward) or +i (inverse)
+template <int DIR>
+__device__ __forceinline__ float2 cquarter(float2 a) {
+  return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft2(float2* v) {
+  float2 t = v[0];
+  v[0] = cadd(t, v[1]);
+  v[1] = csub(t, v[1]);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft4(float2* v) {
+  float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+  float2 b0 = cadd(v[1], v[3]), b1 = cquarter<DIR>(csub(v[1], v[3]));
+  v[0] = cadd(a0, b0);
+  v[2] = csub(a0, b0);
+  v[1] = cadd(a1, b1);
+  v[3] = csub(a1, b1);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft8(float2* v) {
+  float2 e[4] = {v[0], v[2], v[4], v[6]};
+  float2 o[4] = {v[1], v[3], v[5], v[7]};
+  dft4<DIR>(e);
+  dft4<DIR>(o);
+  const float r = 0.70710678118654752440f;
+  // o[k] *= exp(DIR * 2 pi i k / 8)
+  if (DIR < 0) {
+    o[1] = make_float2((o[1].x + o[1].y) * r, (o[1].y - o[1].x) * r);
+    o[3] = make_float2((o[3].y - o[3].x) * r, -(o[3].x + o[3].y) * r);
+  } else {
+    o[1] = make_float2((o[1].x - o[1].y) * r, (o[1].x + o[1].y) * r);
+    o[3] = make_float2(-(o[3].x + o[3].y) * r, (o[3].x - o[3].y) * r);
+  }
+  o[2] = cquarter<DIR>(o[2]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = cadd(e[k], o[k]);
+    v[k + 4] = csub(e[k], o[k]);
+  }
+}
+
+template <int R, int DIR>
+__device__ __forceinline__ void dftR(float2* v) {
+  if (R == 2) dft2<DIR>(v);
+  else if (R == 4) dft4<DIR>(v);
+  else dft8<DIR>(v);
+}
+
+// Lane mask of the team that lane `lane` belongs to.
+template <int T>
+__device__ __forceinline__ unsigned team_mask(int lane) {
+  if (T >= 32) return 0xffffffffu;
+  unsigned m = (T == 32) ? 0xffffffffu : ((1u << T) - 1u);
+  return m << (lane & ~(T - 1));
+}
+
+template <int L, int R, int NS, int T, int DIR, int TWS>
+__device__ __forceinline__ void stockham_pass(float2* x, int t, unsigned mask, const float2* tw) {
+  constexpr int NB = L / R;                 // butterflies in this pass
+  constexpr int PER = (NB + T - 1) / T;     // butterflies per lane
+  float2 v[PER][R];
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int j = t + b * T;
+    if (NB % T == 0 || j < NB) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = x[j + r * NB];
+    }
+  }
+  __syncwarp(mask);
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int j = t + b * T;
+    if (NB % T == 0 || j < NB) {
+      const int k = j & (NS - 1);
+      if (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[(r * k * (L / (NS * R))) * TWS];
+          if (DIR > 0) w.y = -w.y;
+          v[b][r] = cmul(v[b][r], w);
+        }
+      }
+      dftR<R, DIR>(v[b]);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[base + r * NS] = v[b][r];
+    }
+  }
+  __syncwarp(mask);
+}
+
+template <int L, int NS, int T, int DIR, int TWS>
+struct FftPasses {
+  __device__ __forceinline__ static void run(float2* x, int t, unsigned mask, const float2* tw) {
+    constexpr int REM = L / NS;
+    constexpr int R = (REM % 8 == 0) ? 8 : ((REM % 4 == 0) ? 4 : 2);
+    stockham_pass<L, R, NS, T, DIR, TWS>(x, t, mask, tw);
+    FftPasses<L, NS * R, T, DIR, TWS>::run(x, t, mask, tw);
+  }
+};
+template <int L, int T, int DIR, int TWS>
+struct FftPasses<L, L, T, DIR, TWS> {
+  __device__ __forceinline__ static void run(float2*, int, unsigned, const float2*) {}
+};
+
+// Transform one row of length L in place; t = lane index within the team.
+template <int L, int T, int DIR, int TWS>
+__device__ __forceinline__ void team_fft(float2* x, int t, unsigned mask, const float2* tw) {
+  FftPasses<L, 1, T, DIR, TWS>::run(x, t, mask, tw);
+}
+
+// Team size used for a row of length L.
+template <int L>
+struct TeamOf {
+  static constexpr int v = (L / 8) >= 32 ? 32 : ((L / 8) >= 1 ? (L / 8) : 1);
+};

@@ -1,0 +1,200 @@
+"""Thin ctypes binding over libmm_b300.so (declared in include/mm_b300.h).
+
+Argument marshalling only: every step of the field evaluation and of the
+time integration runs in the library's CUDA kernels.  Device arrays are torch
+tensors (float32, contiguous, on the context's device); host arrays are numpy
+arrays.  The library is required: importing this module without it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmm_b300.so")
+
+MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ETIMEOUT, MM_ENONFINITE, MM_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "MM_OK", -1: "MM_EINVAL", -2: "MM_ENOMEM", -3: "MM_ECUDA", -4: "MM_ETIMEOUT",
+                -5: "MM_ENONFINITE", -6: "MM_EUNSUPPORTED"}
+MM_FP32, MM_SPLIT_BF16, MM_SPLIT_FP16 = 0, 1, 2
+MM_RK4, MM_EULER = 0, 1
+TERM_EXCHANGE, TERM_ANISOTROPY, TERM_DEMAG, TERM_ZEEMAN, TERM_ALL = 1, 2, 4, 8, 15
+
+
+class MMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("integrator", ctypes.c_int), ("self_term", ctypes.c_int),
+                ("obs_every", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGNATURES = {
+    "mm_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "mm_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_I), _D, _D, _D, _D, _D, _D, ctypes.POINTER(Opts)]),
+    "mm_destroy": (None, [_P]),
+    "mm_set_stream": (_I, [_P, _P]),
+    "mm_padded_dims": (_I, [_P, ctypes.POINTER(_I)]),
+    "mm_set_m": (_I, [_P, _P]),
+    "mm_get_m": (_I, [_P, _P]),
+    "mm_set_field": (_I, [_P, ctypes.POINTER(_D), _P, _P]),
+    "mm_set_alpha": (_I, [_P, _D]),
+    "mm_heff": (_I, [_P, _P, ctypes.c_uint]),
+    "mm_step": (_I, [_P, _I, _D]),
+    "mm_energy": (_I, [_P, ctypes.POINTER(_D)]),
+    "mm_observables": (_I, [_P, ctypes.POINTER(_D)]),
+    "mm_step_timed": (_I, [_P, _I, _D, ctypes.POINTER(_D)]),
+    "mm_launch_count": (ctypes.c_longlong, [_P]),
+    "mm_sync": (_I, [_P]),
+    "mm_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing; build it with `python -m paper_1501_07293_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a) -> int:
+    """Raw address of a torch tensor (device or host) or a numpy array (host)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy arrays must be C-contiguous float32")
+        return a.ctypes.data
+    if not a.is_contiguous() or str(a.dtype) != "torch.float32":
+        raise ValueError("tensors must be contiguous float32")
+    return a.data_ptr()
+
+
+class Solver:
+    """One film on one GPU: owns an mm_ctx."""
+
+    def __init__(self, grid: Sequence[int], delta: float, Ms: float, A: float, Ku: float, alpha: float,
+                 gamma: float, integrator: str = "rk4", self_term: bool = True, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.grid = tuple(int(g) for g in grid)
+        self.N = self.grid[0] * self.grid[1] * self.grid[2]
+        L = lib()
+        o = Opts()
+        L.mm_default_opts(ctypes.byref(o))
+        o.integrator = MM_EULER if integrator == "euler" else MM_RK4
+        o.self_term = 1 if self_term else 0
+        with torch.cuda.device(self.device):
+            s = torch.cuda.current_stream() if stream is None else stream
+            o.stream = s.cuda_stream
+            self._stream = s
+            ctx = _P()
+            g = (_I * 3)(*self.grid)
+            rc = L.mm_create(ctypes.byref(ctx), g, float(delta), float(Ms), float(A), float(Ku), float(alpha),
+                             float(gamma), ctypes.byref(o))
+            if rc != MM_OK:
+                raise MMError(rc, L.mm_last_error(None).decode())
+        self.ctx = ctx
+        self._L = L
+
+    # -- helpers --------------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != MM_OK:
+            raise MMError(rc, self._L.mm_last_error(self.ctx).decode())
+
+    def _vec_shape(self):
+        nx, ny, nz = self.grid
+        return (3, nz, ny, nx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self._L.mm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- C ABI wrappers -----------------------------------------------------
+    def padded_dims(self):
+        p = (_I * 3)()
+        self._check(self._L.mm_padded_dims(self.ctx, p))
+        return tuple(p)
+
+    def set_m(self, m):
+        """m: (3, nz, ny, nx) float32, torch (device or host) or numpy (host)."""
+        self._check(self._L.mm_set_m(self.ctx, _ptr(m)))
+
+    def get_m(self, out=None):
+        t = self.torch
+        if out is None:
+            out = t.empty(self._vec_shape(), dtype=t.float32, device=self.device)
+        self._check(self._L.mm_get_m(self.ctx, _ptr(out)))
+        return out
+
+    def set_field(self, b_ext=(0.0, 0.0, 0.0), h_map=None, ku_map=None):
+        b = (_D * 3)(*[float(v) for v in b_ext])
+        self._keep = (h_map, ku_map)  # the library copies; keep host buffers alive until then
+        self._check(self._L.mm_set_field(self.ctx, b, None if h_map is None else _ptr(h_map),
+                                         None if ku_map is None else _ptr(ku_map)))
+
+    def set_alpha(self, alpha: float):
+        self._check(self._L.mm_set_alpha(self.ctx, float(alpha)))
+
+    def heff(self, mask: int = TERM_ALL, out=None):
+        t = self.torch
+        if out is None:
+            out = t.empty(self._vec_shape(), dtype=t.float32, device=self.device)
+        self._check(self._L.mm_heff(self.ctx, _ptr(out), int(mask)))
+        return out
+
+    def step(self, n: int, dt: float):
+        self._check(self._L.mm_step(self.ctx, int(n), float(dt)))
+
+    def step_timed(self, n: int, dt: float) -> np.ndarray:
+        """Eager, event-bracketed steps; device ms per kernel class [x-fwd, y/z, x-inv+LLG]."""
+        ms = (_D * 3)(0.0, 0.0, 0.0)
+        self._check(self._L.mm_step_timed(self.ctx, int(n), float(dt), ms))
+        return np.array(ms[:])
+
+    def energy(self) -> np.ndarray:
+        e = (_D * 5)()
+        self._check(self._L.mm_energy(self.ctx, e))
+        return np.array(e[:])
+
+    def observables(self) -> np.ndarray:
+        o = (_D * 5)()
+        self._check(self._L.mm_observables(self.ctx, o))
+        return np.array(o[:])
+
+    def launch_count(self) -> int:
+        return int(self._L.mm_launch_count(self.ctx))
+
+    def sync(self):
+        self._check(self._L.mm_sync(self.ctx))

@@ -1,0 +1,138 @@
+"""Effective-field parity: CUDA path (mm_heff through the C ABI) vs the FP64 oracle.
+
+Bar (FP32 path): relative L2 error <= 1e-5 per field term and for the sum,
+over all cells and components, the oracle evaluated on the same float32
+state the GPU holds.
+"""
+import numpy as np
+import pytest
+
+from oracle.demag import demag_at_cells
+from oracle.llg import TERM_ALL, TERM_ANISOTROPY, TERM_DEMAG, TERM_EXCHANGE, TERM_ZEEMAN
+from paper_1501_07293_b300 import inputs
+
+from _util import gpu_heff, make_film, make_solver, rel_l2, to_device, to_xyz
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+TERMS = [TERM_EXCHANGE, TERM_ANISOTROPY, TERM_DEMAG, TERM_ZEEMAN, TERM_ALL]
+
+# small grids: several tiles along y, ragged tails, degenerate axes, odd sizes
+GRIDS = [(40, 10, 1), (7, 5, 3), (1, 1, 1), (2, 1, 1), (1, 9, 1), (1, 1, 7), (9, 1, 1), (16, 8, 2), (5, 130, 3), (3, 300, 1),
+         (33, 17, 5), (64, 32, 4), (3, 40, 2), (100, 3, 16), (48, 48, 9)]
+
+
+def _compare(grid, delta=4e-9, Ku=5e4, b_ext=(0.01, -0.02, 0.005), seed=7, self_term=True,
+             hmap=False, kumap=False):
+    m = inputs.random_state(grid, seed)
+    hm = inputs.zeeman_map(grid, seed + 1) if hmap else None
+    km = inputs.ku_map(grid, seed + 2) if kumap else None
+    s = make_solver(grid, delta, Ku=Ku, self_term=self_term)
+    import torch
+    s.set_field(b_ext, None if hm is None else torch.from_numpy(hm).cuda(),
+                None if km is None else torch.from_numpy(km).cuda())
+    film = make_film(grid, delta, Ku=Ku, b_ext=b_ext, h_map_dev=hm, ku_map_dev=km, self_term=self_term)
+    mo = to_xyz(m)
+    out = {}
+    for t in TERMS:
+        Hg = gpu_heff(s, m, t)
+        Ho = to_device(film.h_eff(mo, t))
+        out[t] = rel_l2(Hg, Ho) if np.linalg.norm(Ho) > 0 else float(np.abs(Hg).max())
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+def test_heff_matches_oracle(grid):
+    err = _compare(grid)
+    for t, e in err.items():
+        assert e <= TOL, (grid, t, e)
+
+
+@pytest.mark.parametrize("grid", [(40, 10, 1), (12, 7, 3)])
+def test_heff_with_maps(grid):
+    err = _compare(grid, hmap=True, kumap=True)
+    for t, e in err.items():
+        assert e <= TOL, (grid, t, e)
+
+
+def test_heff_without_self_term():
+    err = _compare((20, 6, 2), self_term=False)
+    for t, e in err.items():
+        assert e <= TOL, (t, e)
+
+
+def test_demag_direct_sum_route():
+    # also against the brute-force eq. 13 (not only the oracle's FFT route)
+    grid = (9, 6, 3)
+    m = inputs.random_state(grid, 3)
+    s = make_solver(grid, 5e-9)
+    Hg = gpu_heff(s, m, TERM_DEMAG)
+    film = make_film(grid, 5e-9, demag="direct")
+    Ho = to_device(film.h_demag(to_xyz(m)))
+    assert rel_l2(Hg, Ho) <= TOL
+
+
+def test_heff_full_size_256x256x16():
+    w = inputs.film_256x256x16()
+    m = inputs.workload_state(w)
+    s = make_solver(w.grid, w.delta, Ms=w.mat.Ms, A=w.mat.A, Ku=w.mat.Ku, alpha=w.mat.alpha)
+    s.set_field(w.b_ext)
+    film = make_film(w.grid, w.delta, Ms=w.mat.Ms, A=w.mat.A, Ku=w.mat.Ku, b_ext=w.b_ext)
+    mo = to_xyz(m)
+    for t in (TERM_DEMAG, TERM_ALL):
+        Hg = gpu_heff(s, m, t)
+        Ho = to_device(film.h_eff(mo, t))
+        assert rel_l2(Hg, Ho) <= TOL, t
+    s.close()
+
+
+def test_heff_full_size_512x512x8_sampled():
+    # full size of the precision study; the oracle evaluates eq. 13 at sampled cells
+    w = inputs.film_512x512x8()
+    m = inputs.workload_state(w)
+    s = make_solver(w.grid, w.delta, Ms=w.mat.Ms, A=w.mat.A)
+    Hg = gpu_heff(s, m, TERM_DEMAG)
+    nx, ny, nz = w.grid
+    cells = [(0, 0, 0), (511, 511, 7), (256, 17, 3), (100, 400, 5), (3, 260, 0)]
+    Ho = demag_at_cells(to_xyz(m), w.mat.Ms, cells)
+    Hgc = np.array([[Hg[a, k, j, i] for a in range(3)] for (i, j, k) in cells])
+    assert np.abs(Hgc - Ho).max() <= TOL * np.abs(Hg).max() * 10
+    assert rel_l2(Hgc, Ho) <= TOL * 10
+    s.close()
+
+
+def test_unsupported_grid_is_refused_cleanly():
+    from paper_1501_07293_b300.solver import MM_EUNSUPPORTED, MMError
+    with pytest.raises(MMError) as e:
+        make_solver((8, 8, 17), 4e-9)
+    assert e.value.code == MM_EUNSUPPORTED
+
+
+def test_bad_arguments_return_einval():
+    from paper_1501_07293_b300.solver import MM_EINVAL, MMError
+    with pytest.raises(MMError) as e:
+        make_solver((0, 8, 1), 4e-9)
+    assert e.value.code == MM_EINVAL
+    s = make_solver((8, 8, 1), 4e-9)
+    with pytest.raises(MMError) as e:
+        s.step(-1, 1e-13)
+    assert e.value.code == MM_EINVAL
+    with pytest.raises(MMError):
+        s.heff(99)
+    s.close()
+
+
+def test_nonfinite_state_is_reported():
+    import torch
+    from paper_1501_07293_b300.solver import MM_ENONFINITE, MMError
+    grid = (8, 4, 1)
+    m = inputs.random_state(grid, 1)
+    m[0, 0, 0, 3] = np.nan
+    s = make_solver(grid, 4e-9)
+    s.set_m(torch.from_numpy(m).cuda())
+    with pytest.raises(MMError) as e:
+        s.sync()
+    assert e.value.code == MM_ENONFINITE
+    s.close()
