@@ -164,6 +164,56 @@ int mm_sync(mm_ctx* ctx);
 /* Text of the last failure of this context ("" if none); ctx NULL gives the last create failure. */
 const char* mm_last_error(const mm_ctx* ctx);
 
+/*
+ * Size of the static device scratch array behind mm_heff_noalloc (32 MiB).
+ * It exists on every GPU that loads the library, for the life of the process.
+ */
+#define MM_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * mm_heff_noalloc -- the effective field of one state, computed without any
+ * device allocation.  The paper has no counterpart: it is a service for
+ * callers that cannot call cudaMalloc, for example code that runs while a
+ * stream is being captured into a CUDA graph (an allocation there breaks the
+ * capture), code whose device memory is handed out by another allocator that
+ * already holds the GPU's free memory, or latency-sensitive code that cannot
+ * afford the device-wide synchronisation cudaMalloc/cudaFree imply.
+ *
+ * It needs no context: from grid = {nx, ny, nz}, delta, Ms, A, Ku (easy axis
+ * x), b_ext = mu0 H_ext (tesla, 3 host doubles) and self_term (1 keeps the
+ * tensor's self offset, as mm_create does by default) it builds the
+ * demagnetising tensor (eq. 10/11) and evaluates, for the unit vectors m_dev
+ * ([3][nz][ny][nx] float32, device, used as given -- not normalised), the
+ * terms of term_mask (MM_TERM_*) into H_dev ([3][nz][ny][nx] float32, A/m,
+ * device).  The result equals mm_heff on a context created with the same
+ * parameters and holding the same state.  Work is enqueued on `stream`
+ * (a cudaStream_t; NULL = legacy default stream) and is asynchronous.
+ *
+ * All intermediate data lives in one file-scope static device array of
+ * MM_NOALLOC_SCRATCH_BYTES; grids whose tensor planes (6 nz px py complex
+ * doubles) plus transformed tables do not fit are refused with
+ * MM_EUNSUPPORTED (128 x 128 x 4 fits; 256 x 256 x 4 does not).  No call
+ * allocates, frees or calls an allocating library routine.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device uses the same array, and
+ * each call writes every byte it later reads, so nothing has to be cleared
+ * between calls; but two calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race on the array and give wrong
+ * results.  Serialise them.
+ *
+ * Errors: MM_EINVAL (NULL pointer, size < 1, bad parameter or mask),
+ * MM_EUNSUPPORTED (too large for the array or for the kernels), MM_ECUDA
+ * (launch failure); mm_noalloc_last_error() describes the last failure.
+ */
+int mm_heff_noalloc(const int grid[3], double delta, double Ms, double A, double Ku,
+                    const double b_ext[3], int self_term, const float* m_dev, float* H_dev,
+                    unsigned term_mask, void* stream);
+
+/* Text of the last mm_heff_noalloc failure ("" if none). */
+const char* mm_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

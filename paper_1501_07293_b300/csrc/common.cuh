@@ -96,6 +96,9 @@ int mm_fail(mm_ctx* c, int code, const char* fmt, ...);
 // setup.cu: build Kh (FP64 tensor, FP64 2D transform, FP32 store) and the twiddles.
 int mm_build_kernel(mm_ctx* c);
 
+// Same set-up into caller-provided buffers (Kc: 6 nz px py double2 scratch); returns kernels launched or < 0.
+int mm_setup_kernel_into(const Dims& d, int self_term, double2* Kc, float* Kh, cudaStream_t s);
+
 // field.cu: launchers (return number of kernels launched, or <0 on launch error)
 int mm_supported(const Dims& d, char* why, int nwhy);
 int launch_field_eval(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw,

@@ -168,3 +168,32 @@ int mm_build_kernel(mm_ctx* c) {
   MM_CK(c, cudaMemcpy(c->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
   return MM_OK;
 }
+
+// Tensor set-up into caller-provided buffers (no allocation, no host copy):
+// Kc = 6 nz px py double2 of scratch, Kh = the output table.  Same kernels as
+// mm_build_kernel.
+int mm_setup_kernel_into(const Dims& d, int self_term, double2* Kc, float* Kh, cudaStream_t s) {
+  const long long plane = (long long)d.px * d.py;
+  const long long total = plane * d.nz;
+  k_tensor<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Kc, d, self_term);
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  int n = 1;
+  if (d.px > 1) {
+    const size_t sm = 2 * sizeof(double2) * d.px;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_fft64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_fft64<<<(unsigned)(6LL * d.nz * d.py), d.px / 2 < 256 ? d.px / 2 : 256, sm, s>>>(Kc, d.px, 1, 0, d.px, 1);
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    ++n;
+  }
+  if (d.py > 1) {
+    const size_t sm = 2 * sizeof(double2) * d.py;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_fft64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_fft64<<<(unsigned)(6LL * d.nz * d.px), d.py / 2 < 256 ? d.py / 2 : 256, sm, s>>>(Kc, d.py, d.px, 1, plane, d.px);
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    ++n;
+  }
+  const long long tot = (long long)d.hx * 6 * d.nz * d.hy;
+  k_extract<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Kc, Kh, d);
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  return n + 1;
+}

@@ -55,6 +55,9 @@ _SIGNATURES = {
     "mm_launch_count": (ctypes.c_longlong, [_P]),
     "mm_sync": (_I, [_P]),
     "mm_last_error": (ctypes.c_char_p, [_P]),
+    "mm_heff_noalloc": (_I, [ctypes.POINTER(_I), _D, _D, _D, _D, ctypes.POINTER(_D), _I, _P, _P,
+                             ctypes.c_uint, _P]),
+    "mm_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 _lib = None
@@ -198,3 +201,23 @@ class Solver:
 
     def sync(self):
         self._check(self._L.mm_sync(self.ctx))
+
+
+def heff_noalloc(grid, delta, Ms, A, Ku, b_ext, m, H, mask: int = TERM_ALL, self_term: bool = True,
+                 stream=None):
+    """mm_heff_noalloc: effective field of the device state m into the device tensor H.
+
+    No context and no device allocation (the library's static scratch array
+    holds every intermediate).  m and H are float32 (3, nz, ny, nx) CUDA
+    tensors; calls that overlap on the GPU race on the shared scratch.
+    """
+    import torch
+    L = lib()
+    g = (_I * 3)(*[int(v) for v in grid])
+    b = (_D * 3)(*[float(v) for v in b_ext])
+    s = torch.cuda.current_stream() if stream is None else stream
+    rc = L.mm_heff_noalloc(g, float(delta), float(Ms), float(A), float(Ku), b, 1 if self_term else 0,
+                           _ptr(m), _ptr(H), int(mask), s.cuda_stream)
+    if rc != MM_OK:
+        raise MMError(rc, L.mm_noalloc_last_error().decode())
+    return H
