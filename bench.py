@@ -3,9 +3,10 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
 
-One step = one classical RK4 step (four effective-field evaluations, each a
-forward x transform, the fused y/z transform + demag product, and the inverse
-x transform fused with exchange, anisotropy, Zeeman, LLG and the RK4 update),
+One step = one classical RK4 step: four effective-field evaluations, each two
+kernels -- k_yz (y transform, the demag product along z, inverse y transform)
+and k_x (inverse x transform fused with exchange, anisotropy, Zeeman, LLG, the
+RK4 update, and the x transform of the next stage's state) --
 on synthetic inputs (seeded random unit vectors).  The L2 cache is flushed
 between timed steps (a 512 MiB write), so every step starts cold.
 
@@ -117,10 +118,9 @@ class ClockSampler:
 def algorithmic_bytes(grid):
     """Compulsory HBM bytes per launch of each kernel class (FP32 RK4 stage).
 
-    x-forward: read m (12 B/cell), write the x-transformed field S
-    y/z:       read S, read the transformed kernel Kh, write S
-    x-inverse: read S, m_stage, m0; accumulator r/w (averaged over the 4
-               stages: 1.5 x 12 B/cell); write the next stage (12 B/cell)
+    yz: read the x-transformed field S and the transformed tensor Kh, write S
+    x:  read S, m_stage, m0; accumulator r/w (averaged over the 4 stages:
+        1.5 x 12 B/cell); write the next stage (12 B/cell) and S
     """
     nx, ny, nz = grid
     N = nx * ny * nz
@@ -131,7 +131,7 @@ def algorithmic_bytes(grid):
     S = hx * 3 * nz * ny * 8
     Kh = hx * 6 * nz * hy * 4
     v = 12 * N
-    return {"xfwd": v + S, "yz": 2 * S + Kh, "xinv": S + v + v + 1.5 * v + v}
+    return {"yz": 2 * S + Kh, "x": S + v + v + 1.5 * v + v + S}
 
 
 def measured_peaks():
@@ -269,15 +269,15 @@ def b300_arm(args, w):
         flush.zero_()
         torch.cuda.synchronize()
         kt += s.step_timed(1, w.dt)
-    per_launch_ms = kt / (4 * nk)
-    names = ["xfwd", "yz", "xinv"]
-    kernels = {"xfwd": "k_xfwd", "yz": "k_yz", "xinv": "k_xinv"}
+    per_launch_ms = {"yz": kt[1] / (4 * nk), "x": kt[2] / (4 * nk)}
+    names = ["yz", "x"]
+    kernels = {"yz": "k_yz", "x": "k_x"}
     alg = algorithmic_bytes(w.grid)
-    dom = names[int(np.argmax(per_launch_ms))]
+    dom = max(names, key=lambda n: per_launch_ms[n])
     peak, peak_kind = measured_peaks()
-    achieved = alg[dom] / (per_launch_ms[names.index(dom)] * 1e-3) / 1e9
-    kernel_table = {n: {"ms_per_launch": float(per_launch_ms[i]), "alg_bytes": float(alg[n]),
-                        "GBps": float(alg[n] / (per_launch_ms[i] * 1e-3) / 1e9)} for i, n in enumerate(names)}
+    achieved = alg[dom] / (per_launch_ms[dom] * 1e-3) / 1e9
+    kernel_table = {n: {"ms_per_launch": float(per_launch_ms[n]), "alg_bytes": float(alg[n]),
+                        "GBps": float(alg[n] / (per_launch_ms[n] * 1e-3) / 1e9)} for n in names}
 
     # ---- end to end through the C ABI with host buffers ----
     m_host = torch.from_numpy(m0.copy()).pin_memory()

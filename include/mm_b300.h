@@ -126,7 +126,9 @@ int mm_heff(mm_ctx* ctx, float* H_dev, unsigned term_mask);
  * Advance n >= 0 steps of size dt with the context's integrator.  One RK4
  * step evaluates the effective field four times; the state is renormalised
  * once after each full step (the paper renormalises after every Euler step).
- * The step sequence is replayed from a captured CUDA graph.
+ * The step sequence is replayed from a captured CUDA graph (two kernels per
+ * field evaluation); a call after mm_set_m / mm_heff / mm_energy /
+ * mm_observables first launches one x-transform of the state.
  */
 int mm_step(mm_ctx* ctx, int n, double dt);
 
@@ -148,10 +150,12 @@ int mm_observables(mm_ctx* ctx, double out[5]);
 /*
  * Profiling variant of mm_step: advance n steps launching every kernel
  * eagerly (no graph) with CUDA events around each launch, and add the device
- * time of each kernel class to ms_out[3]: [0] x-forward transforms, [1] y/z
- * transforms with the demag product, [2] x-inverse transforms with the
- * field/LLG update.  ms_out is host memory, accumulated into (not cleared).
- * Same numerical result as mm_step.  Synchronises after every step.
+ * time of each kernel class to ms_out[3]: [0] the x-forward transform that
+ * (re)starts the pipeline after mm_set_m / mm_heff / mm_energy (not part of a
+ * step), [1] y/z transforms with the demag product, [2] x-inverse transforms
+ * with the field/LLG update and the x-forward transform of the new state.
+ * ms_out is host memory, accumulated into (not cleared).  Same numerical
+ * result as mm_step.  Synchronises after every step.
  */
 int mm_step_timed(mm_ctx* ctx, int n, double dt, double ms_out[3]);
 

@@ -193,6 +193,7 @@ extern "C" int mm_set_m(mm_ctx* c, const float* m) {
   if (!c) return MM_EINVAL;
   if (!m) return mm_fail(c, MM_EINVAL, "mm_set_m: m is NULL");
   c->cur = 0;
+  c->s_valid = 0;
   MM_CK(c, cudaMemcpyAsync(c->m0, m, sizeof(float) * 3 * (size_t)c->d.N, cudaMemcpyDefault, c->stream));
   if (launch_normalise(c->d, c->m0, c->dflag, c->stream) < 0) return mm_fail(c, MM_ECUDA, "normalise launch failed");
   c->launches++;
@@ -263,13 +264,16 @@ extern "C" int mm_heff(mm_ctx* c, float* H, unsigned mask) {
   a.H_out = H;
   a.mode = 0;
   a.mask = mask;
-  const int k = launch_field_eval(c->d, make_phys(c), a, c->tw, c->S, c->Kh, c->stream);
+  const int k = launch_field_eval(c->d, make_phys(c), a, c->tw, c->S, c->Kh, c->dflag, c->stream);
+  c->s_valid = 0;
   if (k < 0) return mm_fail(c, MM_ECUDA, "field kernels failed to launch (%d): %s", k, cudaGetErrorString(cudaGetLastError()));
   c->launches += k;
   return MM_OK;
 }
 
 // Enqueue one step on stream s; `from` = buffer holding the state (Euler alternates).
+// S must hold the x transform of that state on entry; it holds the transform of
+// the new state on exit.
 static int enqueue_step(mm_ctx* c, cudaStream_t s, double dt, int from, long long* nk) {
   const Phys ph = make_phys(c);
   StageArgs a = base_args(c);
@@ -279,7 +283,7 @@ static int enqueue_step(mm_ctx* c, cudaStream_t s, double dt, int from, long lon
     a.mode = 2;
     a.m_in = from ? c->stA : c->m0;
     a.m_out = from ? c->m0 : c->stA;
-    const int k = launch_field_eval(c->d, ph, a, c->tw, c->S, c->Kh, s);
+    const int k = launch_stage(c->d, ph, a, c->tw, c->S, c->Kh, c->dflag, s);
     if (k < 0) return k;
     *nk += k;
     return 0;
@@ -293,11 +297,21 @@ static int enqueue_step(mm_ctx* c, cudaStream_t s, double dt, int from, long lon
     a.stage = s4;
     a.m_in = in[s4];
     a.m_out = outp[s4];
-    const int k = launch_field_eval(c->d, ph, a, c->tw, c->S, c->Kh, s);
+    const int k = launch_stage(c->d, ph, a, c->tw, c->S, c->Kh, c->dflag, s);
     if (k < 0) return k;
     *nk += k;
   }
   return 0;
+}
+
+// Make S the x transform of the current state (after mm_set_m, mm_heff, ...).
+static int ensure_spectrum(mm_ctx* c) {
+  if (c->s_valid) return MM_OK;
+  if (launch_xfwd(c->d, state_ptr(c), c->tw, c->S, c->stream) < 0)
+    return mm_fail(c, MM_ECUDA, "x-transform launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  c->launches++;
+  c->s_valid = 1;
+  return MM_OK;
 }
 
 static int build_graphs(mm_ctx* c, double dt) {
@@ -333,6 +347,10 @@ extern "C" int mm_step(mm_ctx* c, int n, double dt) {
     const int r = build_graphs(c, dt);
     if (r != MM_OK) return r;
   }
+  {
+    const int r = ensure_spectrum(c);
+    if (r != MM_OK) return r;
+  }
   for (int i = 0; i < n; ++i) {
     const int g = c->opts.integrator == MM_EULER ? c->cur : 0;
     MM_CK(c, cudaGraphLaunch(c->graph[g], c->stream));
@@ -356,6 +374,16 @@ extern "C" int mm_step_timed(mm_ctx* c, int n, double dt, double ms_out[3]) {
       return mm_fail(c, MM_ECUDA, "event creation failed");
     }
   int rc = MM_OK;
+  if (!c->s_valid) {
+    cudaEventRecord(ev[0], c->stream);
+    rc = ensure_spectrum(c);
+    cudaEventRecord(ev[1], c->stream);
+    if (rc == MM_OK && cudaEventSynchronize(ev[1]) == cudaSuccess) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      ms_out[0] += ms;
+    }
+  }
   for (int step = 0; step < n && rc == MM_OK; ++step) {
     StageArgs a = base_args(c);
     a.dt = (float)dt;
@@ -373,17 +401,19 @@ extern "C" int mm_step_timed(mm_ctx* c, int n, double dt, double ms_out[3]) {
       a.acc = c->acc;
     }
     int ne = 0;
+    int cls[12];
     cudaEventRecord(ev[ne++], c->stream);
     for (int s4 = 0; s4 < nst && rc == MM_OK; ++s4) {
       a.stage = s4;
       a.m_in = in[s4];
       a.m_out = outp[s4];
-      for (int part = 0; part < 3; ++part) {
-        if (launch_field_part(c->d, ph, a, c->tw, c->S, c->Kh, c->stream, part) < 0) {
+      for (int part = 1; part < 3; ++part) {
+        if (launch_field_part(c->d, ph, a, c->tw, c->S, c->Kh, c->dflag, c->stream, part) < 0) {
           rc = mm_fail(c, MM_ECUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
           break;
         }
         c->launches++;
+        cls[ne - 1] = part;
         cudaEventRecord(ev[ne++], c->stream);
       }
     }
@@ -395,7 +425,7 @@ extern "C" int mm_step_timed(mm_ctx* c, int n, double dt, double ms_out[3]) {
     for (int k = 1; k < ne; ++k) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ev[k - 1], ev[k]);
-      ms_out[(k - 1) % 3] += ms;
+      ms_out[cls[k - 1]] += ms;
     }
     if (c->opts.integrator == MM_EULER) c->cur ^= 1;
     c->steps++;
@@ -408,8 +438,9 @@ static int check_flag(mm_ctx* c) {
   int h[4];
   MM_CK(c, cudaMemcpyAsync(h, c->dflag, sizeof h, cudaMemcpyDeviceToHost, c->stream));
   MM_CK(c, cudaStreamSynchronize(c->stream));
-  if (h[0]) {
+  if (h[0] || h[1]) {
     cudaMemsetAsync(c->dflag, 0, sizeof(int) * 4, c->stream);
+    if (h[1]) return mm_fail(c, MM_ETIMEOUT, "a bounded wait inside a kernel gave up (bulk copy did not complete)");
     return mm_fail(c, MM_ENONFINITE, "non-finite or zero magnetisation vector found");
   }
   return MM_OK;
@@ -422,7 +453,8 @@ static int run_reduce(mm_ctx* c, double* host) {
   a.mode = 0;
   a.mask = MM_TERM_DEMAG;
   const Phys ph = make_phys(c);
-  int k = launch_field_eval(c->d, ph, a, c->tw, c->S, c->Kh, c->stream);
+  int k = launch_field_eval(c->d, ph, a, c->tw, c->S, c->Kh, c->dflag, c->stream);
+  c->s_valid = 0;
   if (k < 0) return mm_fail(c, MM_ECUDA, "field kernels failed to launch");
   c->launches += k;
   k = launch_reduce(c->d, ph, state_ptr(c), c->Hs, c->hmap, c->kumap, c->A, c->Ku, c->delta, c->Ms, c->red,

@@ -71,8 +71,9 @@ struct mm_ctx {
   double* red;               // reduction partials
   double* red_out;           // final reduction result (device)
   int red_blocks;
-  int* dflag;                // device error flags: [0] non-finite state
+  int* dflag;                // device error flags: [0] non-finite state, [1] kernel wait timed out
   int cur;                   // Euler: 0 -> state in m0, 1 -> state in stA
+  int s_valid;               // S holds the x transform of the current state
   cudaGraphExec_t graph[2];  // RK4: graph[0]; Euler: graph[0] (m0->stA), graph[1] (stA->m0)
   int graph_valid;
   double graph_dt;
@@ -101,11 +102,17 @@ int mm_setup_kernel_into(const Dims& d, int self_term, double2* Kc, float* Kh, c
 
 // field.cu: launchers (return number of kernels launched, or <0 on launch error)
 int mm_supported(const Dims& d, char* why, int nwhy);
+// flag: device error flags ([1] <- a bounded wait inside a kernel gave up)
 int launch_field_eval(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw,
-                      float2* S, const float* Kh, cudaStream_t s);
+                      float2* S, const float* Kh, int* flag, cudaStream_t s);
+// S holds the x transform of a.m_in: y/z + x inverse/update/forward (2 launches)
+int launch_stage(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
+                 const float* Kh, int* flag, cudaStream_t s);
+// S <- x transform of m (1 launch)
+int launch_xfwd(const Dims& d, const float* m, const float2* tw, float2* S, cudaStream_t s);
 // part: 0 = x-forward, 1 = y/z + product, 2 = x-inverse + update (one launch each)
 int launch_field_part(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
-                      const float* Kh, cudaStream_t s, int part);
+                      const float* Kh, int* flag, cudaStream_t s, int part);
 int launch_normalise(const Dims& d, float* m, int* flag, cudaStream_t s);
 
 // reduce.cu

@@ -9,7 +9,9 @@
 // DIR = -1 is the forward transform exp(-2 pi i nk/L), DIR = +1 the
 // unnormalised inverse.  Twiddles come from a table tw[m] = exp(-2 pi i m/LT)
 // of length LT = L * TWS (TWS a power-of-two stride), so one table serves a
-// transform and its half-length sub-transforms.
+// transform and its half-length sub-transforms.  With PADS > 0 element e of a
+// row is stored at e + (e >> PADS) (one spare slot every 2^PADS elements),
+// which spreads the radix-8 stores of the first passes over all banks.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -83,8 +85,18 @@ __device__ __forceinline__ unsigned team_mask(int lane) {
   return m << (lane & ~(T - 1));
 }
 
-template <int L, int R, int NS, int T, int DIR, int TWS>
-__device__ __forceinline__ void stockham_pass(float2* x, int t, unsigned mask, const float2* tw) {
+template <int PADS>
+__device__ __forceinline__ int pidx(int e) {
+  return PADS > 0 ? e + (e >> PADS) : e;
+}
+
+// One pass.  PADR / PADW: padding of the layout read / written (they differ
+// only when a transform converts between a dense and a padded row).  Inputs at
+// positions >= nin are taken as zero without being read, outputs at positions
+// >= nout are not written (zero padding and truncation of eq. 14).
+template <int L, int R, int NS, int T, int DIR, int TWS, int PADR, int PADW>
+__device__ __forceinline__ void stockham_pass(float2* x, int t, unsigned mask, const float2* tw, int nin,
+                                              int nout) {
   constexpr int NB = L / R;                 // butterflies in this pass
   constexpr int PER = (NB + T - 1) / T;     // butterflies per lane
   float2 v[PER][R];
@@ -93,7 +105,10 @@ __device__ __forceinline__ void stockham_pass(float2* x, int t, unsigned mask, c
     const int j = t + b * T;
     if (NB % T == 0 || j < NB) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = x[j + r * NB];
+      for (int r = 0; r < R; ++r) {
+        const int e = j + r * NB;
+        v[b][r] = (e < nin) ? x[pidx<PADR>(e)] : make_float2(0.f, 0.f);
+      }
     }
   }
   __syncwarp(mask);
@@ -103,40 +118,63 @@ __device__ __forceinline__ void stockham_pass(float2* x, int t, unsigned mask, c
     if (NB % T == 0 || j < NB) {
       const int k = j & (NS - 1);
       if (NS > 1) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 w = tw[(r * k * (L / (NS * R))) * TWS];
-          if (DIR > 0) w.y = -w.y;
-          v[b][r] = cmul(v[b][r], w);
+        // w^r for r = 1..R-1 from one table entry (powers by multiplication:
+        // one shared-memory load per butterfly instead of R-1)
+        float2 wp[8];
+        wp[1] = tw[(k * (L / (NS * R))) * TWS];
+        if (DIR > 0) wp[1].y = -wp[1].y;
+        if (R > 2) { wp[2] = cmul(wp[1], wp[1]); wp[3] = cmul(wp[2], wp[1]); }
+        if (R > 4) {
+          wp[4] = cmul(wp[2], wp[2]);
+          wp[5] = cmul(wp[4], wp[1]);
+          wp[6] = cmul(wp[4], wp[2]);
+          wp[7] = cmul(wp[4], wp[3]);
         }
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], wp[r]);
       }
       dftR<R, DIR>(v[b]);
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) x[base + r * NS] = v[b][r];
+      for (int r = 0; r < R; ++r) {
+        const int e = base + r * NS;
+        if (e < nout) x[pidx<PADW>(e)] = v[b][r];
+      }
     }
   }
   __syncwarp(mask);
 }
 
-template <int L, int NS, int T, int DIR, int TWS>
+// Passes from sub-length NS on.  PIN: padding of the input layout (first pass),
+// PMID: between passes, POUT: of the output layout (last pass).
+template <int L, int NS, int T, int DIR, int TWS, int PIN, int PMID, int POUT>
 struct FftPasses {
-  __device__ __forceinline__ static void run(float2* x, int t, unsigned mask, const float2* tw) {
+  __device__ __forceinline__ static void run(float2* x, int t, unsigned mask, const float2* tw, int nin, int nout) {
     constexpr int REM = L / NS;
     constexpr int R = (REM % 8 == 0) ? 8 : ((REM % 4 == 0) ? 4 : 2);
-    stockham_pass<L, R, NS, T, DIR, TWS>(x, t, mask, tw);
-    FftPasses<L, NS * R, T, DIR, TWS>::run(x, t, mask, tw);
+    constexpr bool first = (NS == 1), last = (NS * R == L);
+    stockham_pass<L, R, NS, T, DIR, TWS, first ? PIN : PMID, last ? POUT : PMID>(x, t, mask, tw,
+                                                                                 first ? nin : L, last ? nout : L);
+    FftPasses<L, NS * R, T, DIR, TWS, PIN, PMID, POUT>::run(x, t, mask, tw, L, nout);
   }
 };
-template <int L, int T, int DIR, int TWS>
-struct FftPasses<L, L, T, DIR, TWS> {
-  __device__ __forceinline__ static void run(float2*, int, unsigned, const float2*) {}
+template <int L, int T, int DIR, int TWS, int PIN, int PMID, int POUT>
+struct FftPasses<L, L, T, DIR, TWS, PIN, PMID, POUT> {
+  __device__ __forceinline__ static void run(float2*, int, unsigned, const float2*, int, int) {}
 };
 
 // Transform one row of length L in place; t = lane index within the team.
-template <int L, int T, int DIR, int TWS>
+template <int L, int T, int DIR, int TWS, int PADS = 0>
 __device__ __forceinline__ void team_fft(float2* x, int t, unsigned mask, const float2* tw) {
-  FftPasses<L, 1, T, DIR, TWS>::run(x, t, mask, tw);
+  FftPasses<L, 1, T, DIR, TWS, PADS, PADS, PADS>::run(x, t, mask, tw, L, L);
+}
+
+// Same, with a dense (PIN) / padded (PMID) / dense (POUT) choice of layouts, only
+// the first nin inputs read (the rest are zeros) and only the first nout outputs
+// written.  A row of length 1 is copied from the input to the output layout.
+template <int L, int T, int DIR, int TWS, int PIN, int PMID, int POUT>
+__device__ __forceinline__ void team_fft_io(float2* x, int t, unsigned mask, const float2* tw, int nin, int nout) {
+  FftPasses<L, 1, T, DIR, TWS, PIN, PMID, POUT>::run(x, t, mask, tw, nin, nout);
 }
 
 // Team size used for a row of length L.

@@ -9,15 +9,22 @@
 //                           Toeplitz sum over the nz planes with the kernel
 //                           transformed along x and y only -- and the inverse
 //                           transform along y, keeping the first ny rows.
-//  k_xinv  (per row tile)   complex-to-real inverse along x (first nx points),
+//  k_x     (per row tile)   complex-to-real inverse along x (first nx points),
 //                           then per cell: demag + exchange (eq. 5, Neumann rule
 //                           eq. 7) + anisotropy (eq. 8) + Zeeman, and either the
 //                           field itself or the LLG right-hand side (eq. 2) with
-//                           the RK4 / Euler update and renormalisation.
+//                           the RK4 / Euler update and renormalisation; when
+//                           stepping it also transforms the new state forward
+//                           along x into S, so that a stage is k_yz + k_x.
 #include <stdio.h>
+
+#include <cooperative_groups.h>
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "bulk.cuh"
+
+namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------------------
 // k_xfwd: CTA = (tile of TY rows along y, plane z, component c)
@@ -80,139 +87,208 @@ __global__ void __launch_bounds__(512) k_xfwd(const float* __restrict__ m, float
 }
 
 // ---------------------------------------------------------------------------
-// k_yz: CTA = one kx column, all 3 components and nz planes in shared memory
+// The product of eq. 14 along z for one (kx, ky) and one output component a:
+//   out[zo] = sum_b sum_zi Kt_{a b}(kx, ky, zo - zi) M_b(zi)
+// Kt at a negative z offset follows from the parity in z, at a mirrored ky
+// (ky > py/2) from the parity in y; the pairs xz, yz hold the imaginary part of
+// their x/y transform and act as i * Kt.  The (zo, zi) block is unrolled (its
+// register indices are static); the loop over b is not, which keeps the code
+// small enough for the instruction cache.  Planes zi >= nz enter as zeros and
+// outputs zo >= nz are never stored, so the FMA block carries no bounds tests.
 // ---------------------------------------------------------------------------
-__constant__ int c_pair[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+template <int NZM>
+__device__ __forceinline__ void zprod(int a, const float2* __restrict__ buf, int rs, int pos, int nz,
+                                      const float* __restrict__ Kk, int hy, int kyf, bool mirrored,
+                                      float2 (&out)[NZM]) {
+#pragma unroll
+  for (int q = 0; q < NZM; ++q) out[q] = make_float2(0.f, 0.f);
+#pragma unroll 1
+  for (int b = 0; b < 3; ++b) {
+    const int p = (a == b) ? a : 2 + a + b;   // xx yy zz | xy xz yz
+    const bool odd_y = (p == 3 || p == 5);
+    const bool odd_z = (p >= 4);              // xz, yz: odd in z and imaginary
+    const float ys = (mirrored && odd_y) ? -1.f : 1.f;
+    const float zs = odd_z ? -ys : ys;
+    const float* kp = Kk + (long long)p * nz * hy + kyf;
+    float kr[NZM], kn[NZM];   // kernel at offsets +q and -q
+    float2 mv[NZM];
+#pragma unroll
+    for (int q = 0; q < NZM; ++q) {
+      const float v = (q < nz) ? __ldg(kp + (long long)q * hy) : 0.f;
+      kr[q] = ys * v;
+      kn[q] = zs * v;
+    }
+#pragma unroll
+    for (int zi = 0; zi < NZM; ++zi) {
+      const float2 v = (zi < nz) ? buf[(b * nz + zi) * rs + pos] : make_float2(0.f, 0.f);
+      mv[zi] = odd_z ? make_float2(-v.y, v.x) : v;   // i * m for the imaginary pairs
+    }
+#pragma unroll
+    for (int zo = 0; zo < NZM; ++zo) {
+#pragma unroll
+      for (int zi = 0; zi < NZM; ++zi) {
+        const float k = (zo >= zi) ? kr[zo - zi] : kn[zi - zo];
+        out[zo].x = fmaf(k, mv[zi].x, out[zo].x);
+        out[zo].y = fmaf(k, mv[zi].y, out[zo].y);
+      }
+    }
+  }
+}
+
+// In-place z product over a column of `len` positions of a shared buffer holding
+// 3 nz planes of stride rs (position q of a plane at posf(q)).  Each warp takes
+// groups of 10 positions with all three output components (lanes 0-29), so every
+// input of a position is read before any output of it is written with only a
+// warp-level barrier in between.
+template <int NZM, int PADS, typename KyOf>
+__device__ __forceinline__ void zprod_column(float2* buf, int rs, int len, int nz, const float* __restrict__ Kk,
+                                             int hy, int py, KyOf ky_of) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int a = lane / 10, kl = lane % 10;
+  const int ntasks = (len + 9) / 10;
+  for (int task = warp; task < ntasks; task += nwarps) {
+    const int k = task * 10 + kl;
+    const bool act = a < 3 && k < len;
+    float2 out[NZM];
+    if (act) {
+      const int ky = ky_of(k);
+      const bool mirrored = ky > py / 2;
+      zprod<NZM>(a, buf, rs, pidx<PADS>(k), nz, Kk, hy, mirrored ? py - ky : ky, mirrored, out);
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int zo = 0; zo < NZM; ++zo)
+        if (zo < nz) buf[(a * nz + zo) * rs + pidx<PADS>(k)] = out[zo];
+    }
+    __syncwarp();
+  }
+}
+
+struct KyIdentity {
+  __device__ int operator()(int k) const { return k; }
+};
+struct KySubband {
+  int q;
+  __device__ int operator()(int k) const { return 2 * k + q; }
+};
+
+// ---------------------------------------------------------------------------
+// k_yz: CTA = one kx column, all 3 components and nz planes in shared memory.
+//  1. the column's 3 nz rows of ny values arrive by bulk copies (TMA engine)
+//     into dense rows of a padded buffer (row stride RS);
+//  2. forward y transform of every row: the first pass reads the dense row and
+//     takes positions >= ny as zeros (zero padding), the later passes use the
+//     padded layout (no shared-memory bank conflicts);
+//  3. the product of eq. 14 along z (zprod_column), in place;
+//  4. inverse y transform; the last pass writes only the first ny outputs, dense;
+//  5. bulk copies back to S.
+// A failed bounded wait sets flag[1] and abandons the column.
+// ---------------------------------------------------------------------------
+template <int PY>
+struct YzLayout {
+  static constexpr int PADS = PY >= 32 ? 4 : 0;
+  static constexpr int RS = PY + (PADS ? PY / 16 : 0) + 2;   // even: rows stay 16-byte aligned
+};
 
 template <int PY, int NZM>
 __global__ void __launch_bounds__(512, 1) k_yz(float2* __restrict__ S, const float* __restrict__ Kh,
-                                                const float2* __restrict__ twY, Dims d) {
+                                                const float2* __restrict__ twY, Dims d, int* flag) {
   constexpr int T = TeamOf<PY>::v;
-  extern __shared__ float2 sm[];
+  constexpr int PADS = YzLayout<PY>::PADS;
+  constexpr int RS = YzLayout<PY>::RS;
+  extern __shared__ __align__(16) float2 sm[];
   float2* tws = sm;        // exp(-2 pi i m / PY), m < PY
-  float2* buf = sm + PY;   // [3 nz][PY]
+  float2* buf = sm + PY;   // [3 nz][RS]
+  __shared__ __align__(8) uint64_t bar;
   const int kx = blockIdx.x;
   const int nz = d.nz, ny = d.ny;
   const int NP = 3 * nz;
   float2* Sk = S + (long long)kx * NP * ny;
+  const bool bulk = (ny % 2) == 0;   // rows of ny float2 are then 16-byte multiples
+  if (bulk) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_arrive_expect_tx(&bar, (uint32_t)(NP * ny * sizeof(float2)));
+      for (int p = 0; p < NP; ++p) bulk_g2s(buf + p * RS, Sk + (long long)p * ny, ny * sizeof(float2), &bar);
+    }
+  } else {
+    for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) buf[(i / ny) * RS + i % ny] = Sk[i];
+  }
   for (int i = threadIdx.x; i < PY; i += blockDim.x) tws[i] = twY[i];
-  for (int i = threadIdx.x; i < NP * PY; i += blockDim.x) {
-    const int p = i / PY, y = i % PY;
-    buf[i] = (y < ny) ? Sk[(long long)p * ny + y] : make_float2(0.f, 0.f);
+  if (bulk && !mbar_wait_bounded(&bar, 0)) {
+    if (threadIdx.x == 0) atomicOr(flag + 1, 1);
+    mbar_wait_bounded(&bar, 0);   // give copies in flight one more bounded chance before leaving
+    return;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int team = threadIdx.x / T, t = threadIdx.x % T, nteams = blockDim.x / T;
   const unsigned mask = team_mask<T>(lane);
   if (PY > 1) {
-    for (int p = team; p < NP; p += nteams) team_fft<PY, T, -1, 1>(buf + p * PY, t, mask, tws);
+    for (int p = team; p < NP; p += nteams)
+      team_fft_io<PY, T, -1, 1, 0, PADS, PADS>(buf + p * RS, t, mask, tws, ny, PY);
     __syncthreads();
   }
-
-  // Product of eq. 14: H_a(kz) = sum_b sum_kz' Kt_ab(kx, ky, kz - kz') M_b(kz').
-  // Each round takes a chunk of ky values and all three output components of
-  // them, so every input of a ky is read before any output of it is written.
-  const float* Kk = Kh + (long long)kx * 6 * nz * d.hy;
-  int chunk = (int)(blockDim.x / 3) & ~31;
-  if (chunk < 1) chunk = (int)(blockDim.x / 3);
-  if (chunk > PY) chunk = PY;
-  const int rounds = (PY + chunk - 1) / chunk;
-  for (int rd = 0; rd < rounds; ++rd) {
-    const int t3 = threadIdx.x;
-    const int a = t3 / chunk;
-    const int ky = rd * chunk + t3 % chunk;
-    const bool act = a < 3 && ky < PY;
-    float2 out[NZM];
-#pragma unroll
-    for (int q = 0; q < NZM; ++q) out[q] = make_float2(0.f, 0.f);
-    if (act) {
-      int kyf = ky;
-      bool mirrored = false;
-      if (ky > PY / 2) { kyf = PY - ky; mirrored = true; }
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const int p = c_pair[a][b];
-        const bool odd_y = (p == 3 || p == 5);
-        const bool odd_z = (p == 4 || p == 5);
-        const bool imag = (p == 4 || p == 5);
-        const float ys = (mirrored && odd_y) ? -1.f : 1.f;
-        float kr[NZM];
-#pragma unroll
-        for (int q = 0; q < NZM; ++q)
-          kr[q] = (q < nz) ? ys * __ldg(Kk + ((long long)p * nz + q) * d.hy + kyf) : 0.f;
-#pragma unroll
-        for (int zi = 0; zi < NZM; ++zi) {
-          if (zi < nz) {
-            float2 mv = buf[(b * nz + zi) * PY + ky];
-            if (imag) mv = cmuli(mv);
-            const float2 mn = odd_z ? make_float2(-mv.x, -mv.y) : mv;  // kernel at negative offset
-#pragma unroll
-            for (int zo = 0; zo < NZM; ++zo) {
-              if (zo < nz) {
-                const float kv = (zo >= zi) ? kr[zo - zi] : kr[zi - zo];
-                const float2 src = (zo >= zi) ? mv : mn;
-                out[zo].x = fmaf(kv, src.x, out[zo].x);
-                out[zo].y = fmaf(kv, src.y, out[zo].y);
-              }
-            }
-          }
-        }
-      }
-    }
-    __syncthreads();
-    if (act) {
-#pragma unroll
-      for (int zo = 0; zo < NZM; ++zo)
-        if (zo < nz) buf[(a * nz + zo) * PY + ky] = out[zo];
-    }
-    __syncthreads();
-  }
-
+  // Product of eq. 14 along z (see zprod).
+  if (PY > 1)
+    zprod_column<NZM, PADS>(buf, RS, PY, nz, Kh + (long long)kx * 6 * nz * d.hy, d.hy, PY, KyIdentity());
+  else
+    zprod_column<NZM, 0>(buf, RS, PY, nz, Kh + (long long)kx * 6 * nz * d.hy, d.hy, PY, KyIdentity());
+  __syncthreads();
   if (PY > 1) {
-    for (int p = team; p < NP; p += nteams) team_fft<PY, T, 1, 1>(buf + p * PY, t, mask, tws);
+    for (int p = team; p < NP; p += nteams)
+      team_fft_io<PY, T, 1, 1, PADS, PADS, 0>(buf + p * RS, t, mask, tws, PY, ny);
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) {
-    const int p = i / ny, y = i % ny;
-    Sk[i] = buf[p * PY + y];
+  if (bulk) {
+    if (threadIdx.x == 0) {
+      fence_proxy_async_smem();
+      for (int p = 0; p < NP; ++p) bulk_s2g(Sk + (long long)p * ny, buf + p * RS, ny * sizeof(float2));
+      bulk_commit();
+      bulk_wait_read_all();
+    }
+  } else {
+    for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) Sk[i] = buf[(i / ny) * RS + i % ny];
   }
 }
 
 // ---------------------------------------------------------------------------
 // per-cell field terms and LLG update
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float3 ld3(const float* __restrict__ m, long long N, long long i) {
-  return make_float3(__ldg(m + i), __ldg(m + i + N), __ldg(m + i + 2 * N));
-}
-
-// plain (coherent) loads for buffers the same kernel also writes
-__device__ __forceinline__ float3 ld3p(const float* m, long long N, long long i) {
-  return make_float3(m[i], m[i + N], m[i + 2 * N]);
-}
-
 __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
   return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
-// Finish one cell given its demag field bd (tesla).
-__device__ __forceinline__ void cell_update(const StageArgs& a, const Phys& ph, const Dims& d,
-                                            int x, int y, int z, float3 bd) {
+// One cell given its demag field bd (tesla).  Mode 0 writes H; modes 1/2 write
+// and return the next stage / new state.
+__device__ __forceinline__ float3 cell_update(const StageArgs& a, const Phys& ph, const Dims& d,
+                                              int x, int y, int z, float3 bd) {
   const long long N = d.N;
   const long long cell = ((long long)z * d.ny + y) * d.nx + x;
-  const float* mi = a.m_in;
-  const float3 m = ld3(mi, N, cell);
+  const float* __restrict__ mi = a.m_in;
   // eq. 5 with eq. 7: a missing neighbour is the cell itself (clamped index)
-  const long long xm = cell - (x > 0 ? 1 : 0), xp = cell + (x < d.nx - 1 ? 1 : 0);
   const long long row = d.nx, pl = (long long)d.nx * d.ny;
-  const long long ym = cell - (y > 0 ? row : 0), yp = cell + (y < d.ny - 1 ? row : 0);
-  const long long zm = cell - (z > 0 ? pl : 0), zp = cell + (z < d.nz - 1 ? pl : 0);
-  float3 lap;
+  const long long nb[6] = {cell - (x > 0 ? 1 : 0), cell + (x < d.nx - 1 ? 1 : 0),
+                           cell - (y > 0 ? row : 0), cell + (y < d.ny - 1 ? row : 0),
+                           cell - (z > 0 ? pl : 0), cell + (z < d.nz - 1 ? pl : 0)};
+  float3 m, lap = make_float3(0.f, 0.f, 0.f);
   {
-    const float3 a1 = ld3(mi, N, xm), a2 = ld3(mi, N, xp), a3 = ld3(mi, N, ym);
-    const float3 a4 = ld3(mi, N, yp), a5 = ld3(mi, N, zm), a6 = ld3(mi, N, zp);
-    lap.x = ((a1.x - m.x) + (a2.x - m.x)) + ((a3.x - m.x) + (a4.x - m.x)) + ((a5.x - m.x) + (a6.x - m.x));
-    lap.y = ((a1.y - m.y) + (a2.y - m.y)) + ((a3.y - m.y) + (a4.y - m.y)) + ((a5.y - m.y) + (a6.y - m.y));
-    lap.z = ((a1.z - m.z) + (a2.z - m.z)) + ((a3.z - m.z) + (a4.z - m.z)) + ((a5.z - m.z) + (a6.z - m.z));
+    float v[3][7];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      v[c][6] = __ldg(mi + cell + c * N);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) v[c][q] = __ldg(mi + nb[q] + c * N);
+    }
+    m = make_float3(v[0][6], v[1][6], v[2][6]);
+    lap.x = ((v[0][0] - m.x) + (v[0][1] - m.x)) + ((v[0][2] - m.x) + (v[0][3] - m.x)) + ((v[0][4] - m.x) + (v[0][5] - m.x));
+    lap.y = ((v[1][0] - m.y) + (v[1][1] - m.y)) + ((v[1][2] - m.y) + (v[1][3] - m.y)) + ((v[1][4] - m.y) + (v[1][5] - m.y));
+    lap.z = ((v[2][0] - m.z) + (v[2][1] - m.z)) + ((v[2][2] - m.z) + (v[2][3] - m.z)) + ((v[2][4] - m.z) + (v[2][5] - m.z));
   }
   const float3 bex = make_float3(ph.c_ex * lap.x, ph.c_ex * lap.y, ph.c_ex * lap.z);
   const float can = a.kumap ? ph.c_an_map * __ldg(a.kumap + cell) : ph.c_an;
@@ -232,7 +308,7 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const Phys& ph, 
     a.H_out[cell] = B.x * ph.inv_mu0;
     a.H_out[cell + N] = B.y * ph.inv_mu0;
     a.H_out[cell + 2 * N] = B.z * ph.inv_mu0;
-    return;
+    return m;
   }
   const float3 B = make_float3(bex.x + ban + bd.x + bz.x, bex.y + bd.y + bz.y, bex.z + bd.z + bz.z);
   // eq. 2 on the unit vector: dm/dt = g1 m x B + g2 m x (m x B)
@@ -246,19 +322,21 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const Phys& ph, 
     nm = make_float3(m.x + a.dt * k.x, m.y + a.dt * k.y, m.z + a.dt * k.z);
     renorm = true;
   } else {
-    const float3 m0 = ld3p(a.m0, N, cell);
+    float* acc = a.acc;
+    const float* m0p = a.m0;
+    const float3 m0 = make_float3(m0p[cell], m0p[cell + N], m0p[cell + 2 * N]);
     if (a.stage == 0) {
-      a.acc[cell] = k.x; a.acc[cell + N] = k.y; a.acc[cell + 2 * N] = k.z;
+      acc[cell] = k.x; acc[cell + N] = k.y; acc[cell + 2 * N] = k.z;
       const float h = 0.5f * a.dt;
       nm = make_float3(m0.x + h * k.x, m0.y + h * k.y, m0.z + h * k.z);
     } else if (a.stage < 3) {
-      float3 s = make_float3(a.acc[cell], a.acc[cell + N], a.acc[cell + 2 * N]);
+      float3 s = make_float3(acc[cell], acc[cell + N], acc[cell + 2 * N]);
       s.x = fmaf(2.f, k.x, s.x); s.y = fmaf(2.f, k.y, s.y); s.z = fmaf(2.f, k.z, s.z);
-      a.acc[cell] = s.x; a.acc[cell + N] = s.y; a.acc[cell + 2 * N] = s.z;
+      acc[cell] = s.x; acc[cell + N] = s.y; acc[cell + 2 * N] = s.z;
       const float h = (a.stage == 1) ? 0.5f * a.dt : a.dt;
       nm = make_float3(m0.x + h * k.x, m0.y + h * k.y, m0.z + h * k.z);
     } else {
-      const float3 s = make_float3(a.acc[cell] + k.x, a.acc[cell + N] + k.y, a.acc[cell + 2 * N] + k.z);
+      const float3 s = make_float3(acc[cell] + k.x, acc[cell + N] + k.y, acc[cell + 2 * N] + k.z);
       const float h = a.dt * (1.0f / 6.0f);
       nm = make_float3(m0.x + h * s.x, m0.y + h * s.y, m0.z + h * s.z);
       renorm = true;
@@ -271,32 +349,49 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const Phys& ph, 
   a.m_out[cell] = nm.x;
   a.m_out[cell + N] = nm.y;
   a.m_out[cell + 2 * N] = nm.z;
+  return nm;
 }
 
 // ---------------------------------------------------------------------------
-// k_xinv: CTA = (tile of TY rows along y, plane z), all three components
+// k_x: CTA = (tile of TY rows along y, plane z), all three components.
+// Inverse x transform of the field (complex-to-real, first nx points), the
+// per-cell update, and -- when `fwd` is set -- the forward x transform of the
+// state just written, stored back into the same tile of S for the next field
+// evaluation (so a stage needs only k_yz2 + k_x).
 // ---------------------------------------------------------------------------
+template <int PADS>
+__device__ __forceinline__ float& rowf(float2* row, int x) {
+  float2& e = row[pidx<PADS>(x >> 1)];
+  return (x & 1) ? e.y : e.x;
+}
+
 template <int HALF>
-__global__ void __launch_bounds__(512) k_xinv(StageArgs a, Phys ph, const float2* __restrict__ S,
-                                              const float2* __restrict__ twP, Dims d, int TY) {
+__global__ void __launch_bounds__(512) k_x(StageArgs a, Phys ph, float2* __restrict__ S,
+                                           const float2* __restrict__ twP, Dims d, int TY, int fwd) {
   const int z = blockIdx.y, y0 = blockIdx.x * TY;
   if constexpr (HALF == 0) {
     for (int r = threadIdx.x; r < TY; r += blockDim.x) {
       const int y = y0 + r;
       if (y >= d.ny) continue;
-      float3 bd;
-      bd.x = ph.c_d * S[((long long)0 * d.nz + z) * d.ny + y].x;
-      bd.y = ph.c_d * S[((long long)1 * d.nz + z) * d.ny + y].x;
-      bd.z = ph.c_d * S[((long long)2 * d.nz + z) * d.ny + y].x;
-      cell_update(a, ph, d, 0, y, z, bd);
+      float2* s0 = S + ((long long)0 * d.nz + z) * d.ny + y;
+      float2* s1 = S + ((long long)1 * d.nz + z) * d.ny + y;
+      float2* s2 = S + ((long long)2 * d.nz + z) * d.ny + y;
+      const float3 bd = make_float3(ph.c_d * s0->x, ph.c_d * s1->x, ph.c_d * s2->x);
+      const float3 nm = cell_update(a, ph, d, 0, y, z, bd);
+      if (fwd) {
+        *s0 = make_float2(nm.x, 0.f);
+        *s1 = make_float2(nm.y, 0.f);
+        *s2 = make_float2(nm.z, 0.f);
+      }
     }
   } else {
     constexpr int T = TeamOf<HALF>::v;
     constexpr int P = 2 * HALF;
-    constexpr int RS = HALF + 2;
+    constexpr int PADS = 4;
+    constexpr int RS = HALF + (HALF + 1) / 16 + 2;
     extern __shared__ float2 sm[];
     float2* tws = sm;
-    float2* rows = sm + P;   // [3][TY] rows of HALF+1 spectrum values
+    float2* rows = sm + P;   // [3][TY] rows, element k at pidx(k), k <= HALF
     for (int i = threadIdx.x; i < P; i += blockDim.x) tws[i] = twP[i];
     const int total = (HALF + 1) * 3 * TY;
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
@@ -305,45 +400,88 @@ __global__ void __launch_bounds__(512) k_xinv(StageArgs a, Phys ph, const float2
       const int y = y0 + r;
       float2 v = make_float2(0.f, 0.f);
       if (y < d.ny) v = S[(((long long)k * 3 + c) * d.nz + z) * d.ny + y];
-      rows[(c * TY + r) * RS + k] = v;
+      rows[(c * TY + r) * RS + pidx<PADS>(k)] = v;
     }
     __syncthreads();
-    // Z[k] = (X[k] + conj X[HALF-k]) + i W_P^{-k} (X[k] - conj X[HALF-k]), k < HALF,
-    // so that the half-length inverse gives P (x[2n] + i x[2n+1]).
+    // Z[k] = (X[k] + conj X[HALF-k]) + i W_P^{-k} (X[k] - conj X[HALF-k]), k < HALF
     const int NR = 3 * TY;
     const int npair = HALF / 2 + 1;
     for (int i = threadIdx.x; i < NR * npair; i += blockDim.x) {
       const int rr = i / npair, k = i % npair;
       float2* row = rows + rr * RS;
       const int k2 = HALF - k;
-      const float2 Xa = row[k], Xb = row[k2];
+      const float2 Xa = row[pidx<PADS>(k)], Xb = row[pidx<PADS>(k2)];
       const float2 w = tws[k];
-      const float2 wm = make_float2(w.x, -w.y);   // W_P^{-k}
+      const float2 wm = make_float2(w.x, -w.y);
       const float2 Za = cadd(cadd(Xa, cconj(Xb)), cmuli(cmul(csub(Xa, cconj(Xb)), wm)));
       if (k == 0 || k == k2) {
-        row[k] = Za;
+        row[pidx<PADS>(k)] = Za;
       } else {
-        const float2 wm2 = make_float2(-w.x, -w.y);  // W_P^{-(HALF-k)} = -W_P^{k}
+        const float2 wm2 = make_float2(-w.x, -w.y);
         const float2 Zb = cadd(cadd(Xb, cconj(Xa)), cmuli(cmul(csub(Xb, cconj(Xa)), wm2)));
-        row[k] = Za;
-        row[k2] = Zb;
+        row[pidx<PADS>(k)] = Za;
+        row[pidx<PADS>(k2)] = Zb;
       }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int team = threadIdx.x / T, t = threadIdx.x % T, nteams = blockDim.x / T;
     const unsigned mask = team_mask<T>(lane);
-    for (int rr = team; rr < NR; rr += nteams) team_fft<HALF, T, 1, 2>(rows + rr * RS, t, mask, tws);
+    for (int rr = team; rr < NR; rr += nteams) team_fft<HALF, T, 1, 2, PADS>(rows + rr * RS, t, mask, tws);
     __syncthreads();
     for (int i = threadIdx.x; i < TY * d.nx; i += blockDim.x) {
       const int r = i / d.nx, x = i % d.nx;
       const int y = y0 + r;
       if (y >= d.ny) continue;
-      float3 bd;
-      bd.x = ph.c_d * reinterpret_cast<const float*>(rows + (0 * TY + r) * RS)[x];
-      bd.y = ph.c_d * reinterpret_cast<const float*>(rows + (1 * TY + r) * RS)[x];
-      bd.z = ph.c_d * reinterpret_cast<const float*>(rows + (2 * TY + r) * RS)[x];
-      cell_update(a, ph, d, x, y, z, bd);
+      float& f0 = rowf<PADS>(rows + (0 * TY + r) * RS, x);
+      float& f1 = rowf<PADS>(rows + (1 * TY + r) * RS, x);
+      float& f2 = rowf<PADS>(rows + (2 * TY + r) * RS, x);
+      const float3 bd = make_float3(ph.c_d * f0, ph.c_d * f1, ph.c_d * f2);
+      const float3 nm = cell_update(a, ph, d, x, y, z, bd);
+      if (fwd) { f0 = nm.x; f1 = nm.y; f2 = nm.z; }
+    }
+    if (!fwd) return;
+    __syncthreads();
+    // zero padding nx..P-1 of every valid row, then the forward half-length transform
+    for (int i = threadIdx.x; i < NR * (P - d.nx); i += blockDim.x) {
+      const int rr = i / (P - d.nx), x = d.nx + i % (P - d.nx);
+      rowf<PADS>(rows + rr * RS, x) = 0.f;
+    }
+    __syncthreads();
+    for (int rr = team; rr < NR; rr += nteams) {
+      if (y0 + rr % TY >= d.ny) continue;
+      team_fft<HALF, T, -1, 2, PADS>(rows + rr * RS, t, mask, tws);
+    }
+    __syncthreads();
+    // X[k] = 1/2 (Z[k] + conj Z[-k]) - i/2 W_P^k (Z[k] - conj Z[-k]), in place by pairs (k, HALF-k)
+    for (int i = threadIdx.x; i < NR * npair; i += blockDim.x) {
+      const int rr = i / npair, k = i % npair;
+      float2* row = rows + rr * RS;
+      const int k2 = HALF - k;
+      if (k == 0) {
+        const float2 z0 = row[pidx<PADS>(0)];
+        row[pidx<PADS>(0)] = make_float2(z0.x + z0.y, 0.f);
+        row[pidx<PADS>(HALF)] = make_float2(z0.x - z0.y, 0.f);
+      } else if (k == k2) {
+        row[pidx<PADS>(k)] = cconj(row[pidx<PADS>(k)]);
+      } else {
+        const float2 zk = row[pidx<PADS>(k)], zc = row[pidx<PADS>(k2)];
+        const float2 w = tws[k];
+        const float2 d1 = csub(zk, cconj(zc));
+        const float2 Xk = cscale(cadd(cadd(zk, cconj(zc)), cmul(make_float2(d1.y, -d1.x), w)), 0.5f);
+        const float2 w2 = make_float2(-w.x, w.y);            // W_P^{HALF-k} = -conj W_P^k
+        const float2 d2 = csub(zc, cconj(zk));
+        const float2 Xc = cscale(cadd(cadd(zc, cconj(zk)), cmul(make_float2(d2.y, -d2.x), w2)), 0.5f);
+        row[pidx<PADS>(k)] = Xk;
+        row[pidx<PADS>(k2)] = Xc;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+      const int r = i % TY, rest = i / TY;
+      const int c = rest % 3, k = rest / 3;
+      const int y = y0 + r;
+      if (y < d.ny) S[(((long long)k * 3 + c) * d.nz + z) * d.ny + y] = rows[(c * TY + r) * RS + pidx<PADS>(k)];
     }
   }
 }
@@ -378,11 +516,29 @@ static int pow2_ceil(int v) {
 static int nzm_of(int nz) { return pow2_ceil(nz); }
 
 static int xtile(int half) { return half <= 256 ? 16 : (half <= 512 ? 8 : 4); }
-static int xinv_tile(int half) { return half <= 128 ? 8 : (half <= 256 ? 8 : (half <= 512 ? 4 : 2)); }
+static int x_tile(int half) { return half <= 256 ? 8 : (half <= 512 ? 4 : 2); }
+static int x_rs(int half) { return half + (half + 1) / 16 + 2; }
 
-static size_t yz_smem(const Dims& d) { return sizeof(float2) * ((size_t)d.py + 3ull * d.nz * d.py); }
+static int yz_rs(int py) { return py + (py >= 32 ? py / 16 : 0) + 2; }
+static size_t yz_smem(const Dims& d) { return sizeof(float2) * ((size_t)d.py + 3ull * d.nz * yz_rs(d.py)); }
+static size_t x_smem(int half) {
+  return half == 0 ? 0 : sizeof(float2) * ((size_t)2 * half + 3ull * x_tile(half) * x_rs(half));
+}
 
 static const size_t kMaxSmem = 227 * 1024;
+
+// Raise a kernel's dynamic shared-memory limit to everything its static shared
+// memory leaves free (once per kernel; a host attribute, not a stream operation).
+template <typename K>
+static cudaError_t allow_max_smem(K kernel, bool& done) {
+  if (done) return cudaSuccess;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxSmem - fa.sharedSizeBytes));
+  if (e == cudaSuccess) done = true;
+  return e;
+}
 
 int mm_supported(const Dims& d, char* why, int nwhy) {
   if (d.px > 2048 || d.py > 2048) {
@@ -393,114 +549,149 @@ int mm_supported(const Dims& d, char* why, int nwhy) {
     snprintf(why, nwhy, "nz = %d > 16 is not supported by the z Toeplitz product of this build", d.nz);
     return 0;
   }
-  if (yz_smem(d) > kMaxSmem) {
+  const size_t need = yz_smem(d);
+  if (need + 64 > kMaxSmem) {   // 64 bytes of static shared memory (the copy barrier)
     snprintf(why, nwhy, "one kx column (3 x nz x py = 3 x %d x %d complex) exceeds shared memory", d.nz, d.py);
     return 0;
   }
   return 1;
 }
 
+// --- x forward (prologue: S <- transform of a state) ------------------------
+template <int HALF>
+static cudaError_t run_xfwd(const Dims& d, const float* m, const float2* tw, float2* S, cudaStream_t s) {
+  const int P = HALF == 0 ? 1 : 2 * HALF;
+  const int TY = HALF == 0 ? 32 : xtile(HALF);
+  const int T = HALF == 0 ? 1 : TeamOf<(HALF > 0 ? HALF : 1)>::v;
+  int threads = HALF == 0 ? 32 : TY * T;
+  if (threads < 32) threads = 32;
+  if (threads > 512) threads = 512;
+  const size_t smem = HALF == 0 ? 0 : sizeof(float2) * ((size_t)P + (size_t)TY * (HALF + 1));
+  static bool attr = false;
+  if (cudaError_t e = allow_max_smem(k_xfwd<HALF>, attr)) return e;
+  dim3 grid((d.ny + TY - 1) / TY, d.nz, 3);
+  k_xfwd<HALF><<<grid, threads, smem, s>>>(m, S, tw + P, d, TY);
+  return cudaGetLastError();
+}
+
+// --- x inverse + update (+ forward of the new state) -------------------------
 template <int HALF>
 static cudaError_t run_x(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
-                         cudaStream_t s, bool fwd) {
+                         cudaStream_t s, int fwd) {
   const int P = HALF == 0 ? 1 : 2 * HALF;
-  const float2* twP = tw + P;
-  if (fwd) {
-    const int TY = HALF == 0 ? 32 : xtile(HALF);
-    const int T = HALF == 0 ? 1 : TeamOf<(HALF > 0 ? HALF : 1)>::v;
-    int threads = HALF == 0 ? 32 : TY * T;
-    if (threads < 32) threads = 32;
-    if (threads > 512) threads = 512;
-    const size_t smem = HALF == 0 ? 0 : sizeof(float2) * ((size_t)P + (size_t)TY * (HALF + 1));
-    static bool attr = false;  // raise the dynamic shared-memory limit once (not a stream operation)
-    if (!attr) { cudaFuncSetAttribute(k_xfwd<HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem); attr = true; }
-    dim3 grid((d.ny + TY - 1) / TY, d.nz, 3);
-    k_xfwd<HALF><<<grid, threads, smem, s>>>(a.m_in, S, twP, d, TY);
-  } else {
-    const int TY = HALF == 0 ? 32 : xinv_tile(HALF);
-    const int T = HALF == 0 ? 1 : TeamOf<(HALF > 0 ? HALF : 1)>::v;
-    int threads = HALF == 0 ? 32 : 3 * TY * T;
-    if (threads < 128) threads = 128;
-    if (threads > 512) threads = 512;
-    const size_t smem = HALF == 0 ? 0 : sizeof(float2) * ((size_t)P + 3ull * TY * (HALF + 2));
-    static bool attr = false;
-    if (!attr) { cudaFuncSetAttribute(k_xinv<HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem); attr = true; }
-    dim3 grid((d.ny + TY - 1) / TY, d.nz, 1);
-    k_xinv<HALF><<<grid, threads, smem, s>>>(a, ph, S, twP, d, TY);
-  }
+  const int TY = HALF == 0 ? 32 : x_tile(HALF);
+  const int T = HALF == 0 ? 1 : TeamOf<(HALF > 0 ? HALF : 1)>::v;
+  int threads = HALF == 0 ? 32 : ((3 * TY + 1) / 2) * T;
+  threads = (threads + 31) / 32 * 32;
+  if (threads < 128) threads = 128;
+  if (threads > 512) threads = 512;
+  static bool attr = false;
+  if (cudaError_t e = allow_max_smem(k_x<HALF>, attr)) return e;
+  dim3 grid((d.ny + TY - 1) / TY, d.nz, 1);
+  k_x<HALF><<<grid, threads, x_smem(HALF), s>>>(a, ph, S, tw + P, d, TY, fwd);
   return cudaGetLastError();
+}
+
+#define MM_HALF_SWITCH(px, CALL)              \
+  switch ((px) == 1 ? 0 : (px) / 2) {         \
+    case 0: return CALL(0);                   \
+    case 2: return CALL(2);                   \
+    case 4: return CALL(4);                   \
+    case 8: return CALL(8);                   \
+    case 16: return CALL(16);                 \
+    case 32: return CALL(32);                 \
+    case 64: return CALL(64);                 \
+    case 128: return CALL(128);               \
+    case 256: return CALL(256);               \
+    case 512: return CALL(512);               \
+    case 1024: return CALL(1024);             \
+  }                                           \
+  return cudaErrorInvalidValue;
+
+static cudaError_t dispatch_xfwd(const Dims& d, const float* m, const float2* tw, float2* S, cudaStream_t s) {
+#define MM_CALL_XFWD(H) run_xfwd<H>(d, m, tw, S, s)
+  MM_HALF_SWITCH(d.px, MM_CALL_XFWD)
+#undef MM_CALL_XFWD
 }
 
 static cudaError_t dispatch_x(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
-                              cudaStream_t s, bool fwd) {
-  switch (d.px == 1 ? 0 : d.px / 2) {
-    case 0: return run_x<0>(d, ph, a, tw, S, s, fwd);
-    case 2: return run_x<2>(d, ph, a, tw, S, s, fwd);
-    case 4: return run_x<4>(d, ph, a, tw, S, s, fwd);
-    case 8: return run_x<8>(d, ph, a, tw, S, s, fwd);
-    case 16: return run_x<16>(d, ph, a, tw, S, s, fwd);
-    case 32: return run_x<32>(d, ph, a, tw, S, s, fwd);
-    case 64: return run_x<64>(d, ph, a, tw, S, s, fwd);
-    case 128: return run_x<128>(d, ph, a, tw, S, s, fwd);
-    case 256: return run_x<256>(d, ph, a, tw, S, s, fwd);
-    case 512: return run_x<512>(d, ph, a, tw, S, s, fwd);
-    case 1024: return run_x<1024>(d, ph, a, tw, S, s, fwd);
-  }
-  return cudaErrorInvalidValue;
+                              cudaStream_t s, int fwd) {
+#define MM_CALL_X(H) run_x<H>(d, ph, a, tw, S, s, fwd)
+  MM_HALF_SWITCH(d.px, MM_CALL_X)
+#undef MM_CALL_X
 }
 
+// --- y/z pass ------------------------------------------------------------------
 template <int PY, int NZM>
-static cudaError_t run_yz_t(const Dims& d, const float2* tw, float2* S, const float* Kh, cudaStream_t s) {
-  const size_t smem = yz_smem(d);
+static cudaError_t run_yz_t(const Dims& d, const float2* tw, float2* S, const float* Kh, int* flag, cudaStream_t s) {
   static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(k_yz<PY, NZM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem); attr = true; }
-  k_yz<PY, NZM><<<d.hx, 512, smem, s>>>(S, Kh, tw + PY, d);
+  if (cudaError_t e = allow_max_smem(k_yz<PY, NZM>, attr)) return e;
+  k_yz<PY, NZM><<<d.hx, 512, yz_smem(d), s>>>(S, Kh, tw + PY, d, flag);
   return cudaGetLastError();
 }
 
+#define MM_NZ_SWITCH(nz, CALL)          \
+  switch (nzm_of(nz)) {                 \
+    case 1: return CALL(1);             \
+    case 2: return CALL(2);             \
+    case 4: return CALL(4);             \
+    case 8: return CALL(8);             \
+    case 16: return CALL(16);           \
+  }                                     \
+  return cudaErrorInvalidValue;
+
 template <int PY>
-static cudaError_t run_yz_nz(const Dims& d, const float2* tw, float2* S, const float* Kh, cudaStream_t s) {
-  switch (nzm_of(d.nz)) {
-    case 1: return run_yz_t<PY, 1>(d, tw, S, Kh, s);
-    case 2: return run_yz_t<PY, 2>(d, tw, S, Kh, s);
-    case 4: return run_yz_t<PY, 4>(d, tw, S, Kh, s);
-    case 8: return run_yz_t<PY, 8>(d, tw, S, Kh, s);
-    case 16: return run_yz_t<PY, 16>(d, tw, S, Kh, s);
-  }
-  return cudaErrorInvalidValue;
+static cudaError_t run_yz_nz(const Dims& d, const float2* tw, float2* S, const float* Kh, int* flag, cudaStream_t s) {
+#define MM_CALL_YZ(Z) run_yz_t<PY, Z>(d, tw, S, Kh, flag, s)
+  MM_NZ_SWITCH(d.nz, MM_CALL_YZ)
+#undef MM_CALL_YZ
 }
 
-static cudaError_t dispatch_yz(const Dims& d, const float2* tw, float2* S, const float* Kh, cudaStream_t s) {
+static cudaError_t dispatch_yz(const Dims& d, const float2* tw, float2* S, const float* Kh, int* flag, cudaStream_t s) {
   switch (d.py) {
-    case 1: return run_yz_nz<1>(d, tw, S, Kh, s);
-    case 4: return run_yz_nz<4>(d, tw, S, Kh, s);
-    case 8: return run_yz_nz<8>(d, tw, S, Kh, s);
-    case 16: return run_yz_nz<16>(d, tw, S, Kh, s);
-    case 32: return run_yz_nz<32>(d, tw, S, Kh, s);
-    case 64: return run_yz_nz<64>(d, tw, S, Kh, s);
-    case 128: return run_yz_nz<128>(d, tw, S, Kh, s);
-    case 256: return run_yz_nz<256>(d, tw, S, Kh, s);
-    case 512: return run_yz_nz<512>(d, tw, S, Kh, s);
-    case 1024: return run_yz_nz<1024>(d, tw, S, Kh, s);
-    case 2048: return run_yz_nz<2048>(d, tw, S, Kh, s);
+    case 1: return run_yz_nz<1>(d, tw, S, Kh, flag, s);
+    case 4: return run_yz_nz<4>(d, tw, S, Kh, flag, s);
+    case 8: return run_yz_nz<8>(d, tw, S, Kh, flag, s);
+    case 16: return run_yz_nz<16>(d, tw, S, Kh, flag, s);
+    case 32: return run_yz_nz<32>(d, tw, S, Kh, flag, s);
+    case 64: return run_yz_nz<64>(d, tw, S, Kh, flag, s);
+    case 128: return run_yz_nz<128>(d, tw, S, Kh, flag, s);
+    case 256: return run_yz_nz<256>(d, tw, S, Kh, flag, s);
+    case 512: return run_yz_nz<512>(d, tw, S, Kh, flag, s);
+    case 1024: return run_yz_nz<1024>(d, tw, S, Kh, flag, s);
+    case 2048: return run_yz_nz<2048>(d, tw, S, Kh, flag, s);
   }
   return cudaErrorInvalidValue;
 }
 
+// Field evaluation from scratch (mode 0): x forward of a.m_in, y/z, x inverse.
 int launch_field_eval(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
-                      const float* Kh, cudaStream_t s) {
-  if (dispatch_x(d, ph, a, tw, S, s, true) != cudaSuccess) return -1;
-  if (dispatch_yz(d, tw, S, Kh, s) != cudaSuccess) return -2;
-  if (dispatch_x(d, ph, a, tw, S, s, false) != cudaSuccess) return -3;
+                      const float* Kh, int* flag, cudaStream_t s) {
+  if (dispatch_xfwd(d, a.m_in, tw, S, s) != cudaSuccess) return -1;
+  if (dispatch_yz(d, tw, S, Kh, flag, s) != cudaSuccess) return -2;
+  if (dispatch_x(d, ph, a, tw, S, s, a.mode != 0) != cudaSuccess) return -3;
   return 3;
 }
 
+// One stage when S already holds the x transform of a.m_in: y/z, then x inverse
+// + update + x forward of the new state (S then holds the transform of a.m_out).
+int launch_stage(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
+                 const float* Kh, int* flag, cudaStream_t s) {
+  if (dispatch_yz(d, tw, S, Kh, flag, s) != cudaSuccess) return -2;
+  if (dispatch_x(d, ph, a, tw, S, s, 1) != cudaSuccess) return -3;
+  return 2;
+}
+
+int launch_xfwd(const Dims& d, const float* m, const float2* tw, float2* S, cudaStream_t s) {
+  return dispatch_xfwd(d, m, tw, S, s) == cudaSuccess ? 1 : -1;
+}
+
 int launch_field_part(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
-                      const float* Kh, cudaStream_t s, int part) {
+                      const float* Kh, int* flag, cudaStream_t s, int part) {
   cudaError_t e = cudaErrorInvalidValue;
-  if (part == 0) e = dispatch_x(d, ph, a, tw, S, s, true);
-  else if (part == 1) e = dispatch_yz(d, tw, S, Kh, s);
-  else if (part == 2) e = dispatch_x(d, ph, a, tw, S, s, false);
+  if (part == 0) e = dispatch_xfwd(d, a.m_in, tw, S, s);
+  else if (part == 1) e = dispatch_yz(d, tw, S, Kh, flag, s);
+  else if (part == 2) e = dispatch_x(d, ph, a, tw, S, s, a.mode != 0);
   return e == cudaSuccess ? 1 : -1;
 }
 

@@ -77,12 +77,13 @@ extern "C" int mm_heff_noalloc(const int grid[3], double delta, double Ms, doubl
   int Lmax = d.px > d.py ? d.px : d.py;
   if (Lmax < 2) Lmax = 2;
 
-  // Scratch layout: [Kh][twiddles][Kc during set-up, then S]  (S reuses Kc's bytes).
+  // Scratch layout: [flags][Kh][twiddles][Kc during set-up, then S]  (S reuses Kc's bytes).
+  const size_t fl_b = 256;
   const size_t kh_b = align256(sizeof(float) * (size_t)d.hx * 6 * d.nz * d.hy);
   const size_t tw_b = align256(sizeof(float2) * 2 * (size_t)Lmax);
   const size_t kc_b = align256(sizeof(double2) * 6 * (size_t)d.nz * d.px * d.py);
   const size_t s_b = align256(sizeof(float2) * (size_t)d.hx * 3 * d.nz * d.ny);
-  const size_t need = kh_b + tw_b + (kc_b > s_b ? kc_b : s_b);
+  const size_t need = fl_b + kh_b + tw_b + (kc_b > s_b ? kc_b : s_b);
   if (need > (size_t)MM_NOALLOC_SCRATCH_BYTES)
     return noalloc_fail(MM_EUNSUPPORTED,
                         "mm_heff_noalloc: grid %d x %d x %d needs %zu bytes of scratch, the static array holds %zu",
@@ -108,11 +109,14 @@ extern "C" int mm_heff_noalloc(const int grid[3], double delta, double Ms, doubl
     }
     base = (unsigned char*)g_scratch_addr[dev];
   }
-  float* Kh = (float*)base;
-  float2* tw = (float2*)(base + kh_b);
-  double2* Kc = (double2*)(base + kh_b + tw_b);
-  float2* S = (float2*)(base + kh_b + tw_b);
+  int* flags = (int*)base;   // kernels' error flags (a bounded wait that gave up sets flags[1])
+  float* Kh = (float*)(base + fl_b);
+  float2* tw = (float2*)(base + fl_b + kh_b);
+  double2* Kc = (double2*)(base + fl_b + kh_b + tw_b);
+  float2* S = (float2*)(base + fl_b + kh_b + tw_b);
   cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(flags, 0, 4 * sizeof(int), s) != cudaSuccess)
+    return noalloc_fail(MM_ECUDA, "mm_heff_noalloc: clearing the flags failed");
 
   k_noalloc_twiddles<<<(2 * Lmax + 255) / 256, 256, 0, s>>>(tw, Lmax);
   if (cudaGetLastError() != cudaSuccess) return noalloc_fail(MM_ECUDA, "mm_heff_noalloc: twiddle launch failed");
@@ -136,7 +140,7 @@ extern "C" int mm_heff_noalloc(const int grid[3], double delta, double Ms, doubl
   a.H_out = H_dev;
   a.mode = 0;
   a.mask = term_mask;
-  if (launch_field_eval(d, ph, a, tw, S, Kh, s) < 0)
+  if (launch_field_eval(d, ph, a, tw, S, Kh, flags, s) < 0)
     return noalloc_fail(MM_ECUDA, "mm_heff_noalloc: field kernels failed to launch: %s",
                         cudaGetErrorString(cudaGetLastError()));
   return MM_OK;

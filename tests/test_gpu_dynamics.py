@@ -117,5 +117,10 @@ def test_launch_count_and_graph_replay():
     before = s.launch_count()
     s.step(5, 1e-13)
     s.sync()
-    assert s.launch_count() - before == 5 * 12   # 4 RK4 stages x 3 kernels per step
+    # one x-transform to start the pipeline, then 4 RK4 stages x 2 kernels per step
+    assert s.launch_count() - before == 1 + 5 * 8
+    before = s.launch_count()
+    s.step(3, 1e-13)
+    s.sync()
+    assert s.launch_count() - before == 3 * 8
     s.close()
