@@ -159,6 +159,31 @@ int mm_observables(mm_ctx* ctx, double out[5]);
  */
 int mm_step_timed(mm_ctx* ctx, int n, double dt, double ms_out[3]);
 
+/*
+ * Gradients of a loss of the final state of an RK4 trajectory (the reverse
+ * mode of the step sequence mm_step runs; the paper has no adjoint, this is
+ * the derivative of its eq. 2 with the fields of eq. 3, 5/7, 8 and 13).
+ *
+ * The trajectory starts from the context's current state m0 and runs n >= 1
+ * steps of size dt with the current applied field and maps; on return the
+ * context holds the final state m_n (as after mm_step(ctx, n, dt)).
+ * dL_dm_final (host or device, [3][nz][ny][nx]) is dL/dm_n.  Outputs (host or
+ * device; NULL skips one):
+ *   dL_dh   [3][nz][ny][nx]  gradient with respect to the per-cell applied
+ *                            field map h (per tesla), whether or not a map is set
+ *   dL_dku  [nz][ny][nx]     gradient with respect to the per-cell Ku (per J/m^3)
+ *   dL_dm0  [3][nz][ny][nx]  gradient with respect to the direction of m0,
+ *                            (I - m0 m0^T) dL/dm0, i.e. through the
+ *                            normalisation that mm_set_m applies
+ * Memory: checkpoints every ckpt_every steps ((n/ckpt_every + 1) states) and
+ * one recomputed segment (8 ckpt_every + 1 vector fields), allocated on the
+ * first call and kept.  Cost: one forward pass, one recomputation, and four
+ * applications of the symmetric exchange + demag operator per step.  RK4 only
+ * (MM_EUNSUPPORTED for Euler).  Asynchronous.
+ */
+int mm_adjoint(mm_ctx* ctx, int n, double dt, int ckpt_every, const float* dL_dm_final,
+               float* dL_dh, float* dL_dku, float* dL_dm0);
+
 /* Number of kernels this context has enqueued so far (graph nodes counted per replay). */
 long long mm_launch_count(const mm_ctx* ctx);
 

@@ -65,6 +65,7 @@ static void free_ctx(mm_ctx* c) {
   cudaFree(c->m0); cudaFree(c->stA); cudaFree(c->stB); cudaFree(c->acc); cudaFree(c->Hs);
   cudaFree(c->hmap); cudaFree(c->kumap); cudaFree(c->S); cudaFree(c->Kh); cudaFree(c->tw);
   cudaFree(c->red); cudaFree(c->red_out); cudaFree(c->dflag);
+  mm_adjoint_free(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->ev) cudaEventDestroy(c->ev);
   free(c);

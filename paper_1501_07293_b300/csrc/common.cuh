@@ -47,6 +47,7 @@ struct StageArgs {
   float* acc;          // RK4 accumulator sum_s w_s k_s
   float* m_out;        // next stage state / new state
   float* H_out;        // mode 0 output (A/m)
+  float* B_out;        // modes 1/2: if set, the total field B (tesla) at m_in is stored here
   const float* hmap;   // per-cell applied field (T) or null
   const float* kumap;  // per-cell Ku (J/m^3) or null
   int mode;
@@ -81,8 +82,16 @@ struct mm_ctx {
   long long graph_nodes[2];
   long long launches;
   long long steps;
+  // adjoint workspace (allocated by the first mm_adjoint, grown on demand)
+  float* adj_ckpt;           // checkpoints [nseg + 1][3N]
+  float* adj_seg;            // stage states [k][4][3N] + end state [3N], then fields [k][4][3N]
+  float* adj_work;           // cotangents and gradient accumulators
+  size_t adj_ckpt_cap, adj_seg_cap, adj_work_cap;   // in floats
   char err[512];
 };
+
+// adjoint.cu
+void mm_adjoint_free(mm_ctx* c);
 
 // Status helpers (api.cu)
 int mm_fail(mm_ctx* c, int code, const char* fmt, ...);

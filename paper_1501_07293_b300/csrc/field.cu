@@ -311,6 +311,11 @@ __device__ __forceinline__ float3 cell_update(const StageArgs& a, const Phys& ph
     return m;
   }
   const float3 B = make_float3(bex.x + ban + bd.x + bz.x, bex.y + bd.y + bz.y, bex.z + bd.z + bz.z);
+  if (a.B_out) {   // recorded for the adjoint sweep
+    a.B_out[cell] = B.x;
+    a.B_out[cell + N] = B.y;
+    a.B_out[cell + 2 * N] = B.z;
+  }
   // eq. 2 on the unit vector: dm/dt = g1 m x B + g2 m x (m x B)
   const float3 mxB = cross3(m, B);
   const float3 mxmxB = cross3(m, mxB);

@@ -52,6 +52,7 @@ _SIGNATURES = {
     "mm_energy": (_I, [_P, ctypes.POINTER(_D)]),
     "mm_observables": (_I, [_P, ctypes.POINTER(_D)]),
     "mm_step_timed": (_I, [_P, _I, _D, ctypes.POINTER(_D)]),
+    "mm_adjoint": (_I, [_P, _I, _D, _I, _P, _P, _P, _P]),
     "mm_launch_count": (ctypes.c_longlong, [_P]),
     "mm_sync": (_I, [_P]),
     "mm_last_error": (ctypes.c_char_p, [_P]),
@@ -185,6 +186,25 @@ class Solver:
         ms = (_D * 3)(0.0, 0.0, 0.0)
         self._check(self._L.mm_step_timed(self.ctx, int(n), float(dt), ms))
         return np.array(ms[:])
+
+    def adjoint(self, n: int, dt: float, ckpt_every: int, dL_dm_final, want=("m0", "h", "ku")):
+        """mm_adjoint from the current state: returns dict of gradients (device tensors).
+
+        On return the solver holds the final state of the n steps.
+        """
+        t = self.torch
+        nx, ny, nz = self.grid
+        out = {}
+        gm0 = t.empty(self._vec_shape(), dtype=t.float32, device=self.device) if "m0" in want else None
+        gh = t.empty(self._vec_shape(), dtype=t.float32, device=self.device) if "h" in want else None
+        gk = t.empty((nz, ny, nx), dtype=t.float32, device=self.device) if "ku" in want else None
+        self._check(self._L.mm_adjoint(self.ctx, int(n), float(dt), int(ckpt_every), _ptr(dL_dm_final),
+                                       None if gh is None else _ptr(gh), None if gk is None else _ptr(gk),
+                                       None if gm0 is None else _ptr(gm0)))
+        for k, v in (("m0", gm0), ("h", gh), ("ku", gk)):
+            if v is not None:
+                out[k] = v
+        return out
 
     def energy(self) -> np.ndarray:
         e = (_D * 5)()
