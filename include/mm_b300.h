@@ -194,6 +194,53 @@ int mm_sync(mm_ctx* ctx);
 const char* mm_last_error(const mm_ctx* ctx);
 
 /*
+ * Batches of independent films (e.g. one film per point of a field sweep),
+ * advanced together.  The paper runs one film; a batch applies the same
+ * per-film method (every entry point above, through mm_batch_film) to many
+ * films of uneven size with few launches: films with equal padded sizes share
+ * one launch per kernel, and the groups run as parallel branches of one CUDA
+ * graph per step.  RK4 only.
+ */
+typedef struct mm_batch mm_batch;
+
+/*
+ * nfilms films; grids = nfilms consecutive {nx, ny, nz} triples (host); shared
+ * material parameters as in mm_create.  Each film starts at m = (1, 0, 0) with
+ * zero applied field.  Synchronises.  *out is NULL on failure (mm_batch_last_error(NULL)).
+ */
+int mm_batch_create(mm_batch** out, int nfilms, const int* grids, double delta, double Ms, double A,
+                    double Ku, double alpha, double gamma, const mm_opts* opts);
+void mm_batch_destroy(mm_batch* b);
+
+/* The context of film f (owned by the batch; do not destroy): mm_set_m, mm_get_m,
+ * mm_set_field, mm_heff, mm_energy, mm_observables work on it. */
+mm_ctx* mm_batch_film(mm_batch* b, int film);
+
+/* Advance every film n steps of size dt. */
+int mm_batch_step(mm_batch* b, int n, double dt);
+
+/*
+ * Advance every film until its max over cells of |dm/dt| (rad/s, eq. 2 at the
+ * state) is below tol_dmdt, checked every check_every steps, or max_steps steps
+ * have been taken.  A film that stops keeps its state from then on.
+ * steps_out (host, nfilms ints, nullable) receives the steps each film took.
+ * Synchronises.
+ */
+int mm_batch_run(mm_batch* b, int max_steps, double dt, double tol_dmdt, int check_every, int* steps_out);
+
+/* max |dm/dt| (rad/s) per film as last recorded (host, nfilms floats).  Synchronises. */
+int mm_batch_max_dmdt(mm_batch* b, float* out);
+
+/* Number of groups of equal padded sizes (= parallel branches of the step graph). */
+int mm_batch_group_count(const mm_batch* b);
+
+/* Kernels enqueued by the batch's own launches so far. */
+long long mm_batch_launch_count(const mm_batch* b);
+
+/* Last failure of this batch ("" if none); NULL gives the last create failure. */
+const char* mm_batch_last_error(const mm_batch* b);
+
+/*
  * Size of the static device scratch array behind mm_heff_noalloc (32 MiB).
  * It exists on every GPU that loads the library, for the life of the process.
  */

@@ -24,7 +24,7 @@ static int pow2_at_least(int v) {
   return p;
 }
 
-static Phys make_phys(const mm_ctx* c) {
+Phys mm_make_phys(const mm_ctx* c) {
   Phys ph;
   const double Ms = c->Ms, dl = c->delta;
   ph.c_ex = (float)(2.0 * c->A / (Ms * dl * dl));
@@ -265,7 +265,7 @@ extern "C" int mm_heff(mm_ctx* c, float* H, unsigned mask) {
   a.H_out = H;
   a.mode = 0;
   a.mask = mask;
-  const int k = launch_field_eval(c->d, make_phys(c), a, c->tw, c->S, c->Kh, c->dflag, c->stream);
+  const int k = launch_field_eval(c->d, mm_make_phys(c), a, c->tw, c->S, c->Kh, c->dflag, c->stream);
   c->s_valid = 0;
   if (k < 0) return mm_fail(c, MM_ECUDA, "field kernels failed to launch (%d): %s", k, cudaGetErrorString(cudaGetLastError()));
   c->launches += k;
@@ -276,7 +276,7 @@ extern "C" int mm_heff(mm_ctx* c, float* H, unsigned mask) {
 // S must hold the x transform of that state on entry; it holds the transform of
 // the new state on exit.
 static int enqueue_step(mm_ctx* c, cudaStream_t s, double dt, int from, long long* nk) {
-  const Phys ph = make_phys(c);
+  const Phys ph = mm_make_phys(c);
   StageArgs a = base_args(c);
   a.dt = (float)dt;
   *nk = 0;
@@ -367,7 +367,7 @@ extern "C" int mm_step_timed(mm_ctx* c, int n, double dt, double ms_out[3]) {
   if (!ms_out) return mm_fail(c, MM_EINVAL, "mm_step_timed: ms_out is NULL");
   if (n < 0) return mm_fail(c, MM_EINVAL, "mm_step_timed: n = %d < 0", n);
   if (!(dt > 0) || dt > 1e-6) return mm_fail(c, MM_EINVAL, "mm_step_timed: dt = %g s out of range", dt);
-  const Phys ph = make_phys(c);
+  const Phys ph = mm_make_phys(c);
   cudaEvent_t ev[13];
   for (int i = 0; i < 13; ++i)
     if (cudaEventCreate(&ev[i]) != cudaSuccess) {
@@ -453,7 +453,7 @@ static int run_reduce(mm_ctx* c, double* host) {
   a.H_out = c->Hs;
   a.mode = 0;
   a.mask = MM_TERM_DEMAG;
-  const Phys ph = make_phys(c);
+  const Phys ph = mm_make_phys(c);
   int k = launch_field_eval(c->d, ph, a, c->tw, c->S, c->Kh, c->dflag, c->stream);
   c->s_valid = 0;
   if (k < 0) return mm_fail(c, MM_ECUDA, "field kernels failed to launch");

@@ -48,6 +48,7 @@ struct StageArgs {
   float* m_out;        // next stage state / new state
   float* H_out;        // mode 0 output (A/m)
   float* B_out;        // modes 1/2: if set, the total field B (tesla) at m_in is stored here
+  float* maxdmdt;      // modes 1/2: if set, max over cells of |dm/dt| at m_in is atomically maxed in
   const float* hmap;   // per-cell applied field (T) or null
   const float* kumap;  // per-cell Ku (J/m^3) or null
   int mode;
@@ -92,6 +93,30 @@ struct mm_ctx {
 
 // adjoint.cu
 void mm_adjoint_free(mm_ctx* c);
+
+// api.cu
+Phys mm_make_phys(const mm_ctx* c);
+
+// One film of a batch, as the batched kernels see it (device array).
+struct BatchFilm {
+  Dims d;
+  Phys ph;
+  float *m0, *stA, *stB, *acc;
+  const float *hmap, *kumap;
+  float2* S;
+  const float* Kh;
+  const float2* tw;
+  float* maxdmdt;   // max |dm/dt| recorded at stage 0 (atomic max of the float bits)
+  int active;       // 0: the film's CTAs return at once
+};
+
+// field.cu: one batched launch over the films of a group with equal padded sizes.
+// kind: 0 = x forward of m0, 1 = y/z + product, 2 = x inverse + RK4 stage + x forward.
+// map[i] = (film, tile) of CTA i; TY = rows per tile of the x kernels (x_batch_tile).
+int launch_batch(const BatchFilm* F, int px, int py, int nzm, const int2* map, int nblocks, size_t smem_yz,
+                 int kind, int stage, float dt, int* flag, cudaStream_t s);
+int x_batch_tile(int px, int kind);
+size_t mm_yz_smem(const Dims& d);
 
 // Status helpers (api.cu)
 int mm_fail(mm_ctx* c, int code, const char* fmt, ...);

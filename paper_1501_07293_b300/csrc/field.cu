@@ -19,6 +19,7 @@
 #include <stdio.h>
 
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -30,9 +31,9 @@ namespace cg = cooperative_groups;
 // k_xfwd: CTA = (tile of TY rows along y, plane z, component c)
 // ---------------------------------------------------------------------------
 template <int HALF>
-__global__ void __launch_bounds__(512) k_xfwd(const float* __restrict__ m, float2* __restrict__ S,
-                                              const float2* __restrict__ twP, Dims d, int TY) {
-  const int c = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * TY;
+__device__ __forceinline__ void body_xfwd(const float* __restrict__ m, float2* __restrict__ S,
+                                          const float2* __restrict__ twP, const Dims& d, int TY, int c, int z,
+                                          int y0) {
   if constexpr (HALF == 0) {
     // px = 1 (nx = 1): the transform along x is the identity.
     for (int r = threadIdx.x; r < TY; r += blockDim.x) {
@@ -84,6 +85,12 @@ __global__ void __launch_bounds__(512) k_xfwd(const float* __restrict__ m, float
       S[(((long long)k * 3 + c) * d.nz + z) * d.ny + y] = X;
     }
   }
+}
+
+template <int HALF>
+__global__ void __launch_bounds__(512) k_xfwd(const float* __restrict__ m, float2* __restrict__ S,
+                                              const float2* __restrict__ twP, Dims d, int TY) {
+  body_xfwd<HALF>(m, S, twP, d, TY, blockIdx.z, blockIdx.y, blockIdx.x * TY);
 }
 
 // ---------------------------------------------------------------------------
@@ -192,8 +199,8 @@ struct YzLayout {
 };
 
 template <int PY, int NZM>
-__global__ void __launch_bounds__(512, 1) k_yz(float2* __restrict__ S, const float* __restrict__ Kh,
-                                                const float2* __restrict__ twY, Dims d, int* flag) {
+__device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __restrict__ Kh,
+                                        const float2* __restrict__ twY, const Dims& d, int* flag, int kx) {
   constexpr int T = TeamOf<PY>::v;
   constexpr int PADS = YzLayout<PY>::PADS;
   constexpr int RS = YzLayout<PY>::RS;
@@ -201,7 +208,6 @@ __global__ void __launch_bounds__(512, 1) k_yz(float2* __restrict__ S, const flo
   float2* tws = sm;        // exp(-2 pi i m / PY), m < PY
   float2* buf = sm + PY;   // [3 nz][RS]
   __shared__ __align__(8) uint64_t bar;
-  const int kx = blockIdx.x;
   const int nz = d.nz, ny = d.ny;
   const int NP = 3 * nz;
   float2* Sk = S + (long long)kx * NP * ny;
@@ -257,6 +263,12 @@ __global__ void __launch_bounds__(512, 1) k_yz(float2* __restrict__ S, const flo
   }
 }
 
+template <int PY, int NZM>
+__global__ void __launch_bounds__(512, 1) k_yz(float2* __restrict__ S, const float* __restrict__ Kh,
+                                                const float2* __restrict__ twY, Dims d, int* flag) {
+  body_yz<PY, NZM>(S, Kh, twY, d, flag, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // per-cell field terms and LLG update
 // ---------------------------------------------------------------------------
@@ -267,7 +279,7 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 // One cell given its demag field bd (tesla).  Mode 0 writes H; modes 1/2 write
 // and return the next stage / new state.
 __device__ __forceinline__ float3 cell_update(const StageArgs& a, const Phys& ph, const Dims& d,
-                                              int x, int y, int z, float3 bd) {
+                                              int x, int y, int z, float3 bd, float* kmag = nullptr) {
   const long long N = d.N;
   const long long cell = ((long long)z * d.ny + y) * d.nx + x;
   const float* __restrict__ mi = a.m_in;
@@ -321,6 +333,7 @@ __device__ __forceinline__ float3 cell_update(const StageArgs& a, const Phys& ph
   const float3 mxmxB = cross3(m, mxB);
   const float3 k = make_float3(ph.g1 * mxB.x + ph.g2 * mxmxB.x, ph.g1 * mxB.y + ph.g2 * mxmxB.y,
                                ph.g1 * mxB.z + ph.g2 * mxmxB.z);
+  if (kmag) *kmag = sqrtf(k.x * k.x + k.y * k.y + k.z * k.z);   // |dm/dt| at m_in
   float3 nm;
   bool renorm = false;
   if (a.mode == 2) {
@@ -371,10 +384,11 @@ __device__ __forceinline__ float& rowf(float2* row, int x) {
 }
 
 template <int HALF>
-__global__ void __launch_bounds__(512) k_x(StageArgs a, Phys ph, float2* __restrict__ S,
-                                           const float2* __restrict__ twP, Dims d, int TY, int fwd) {
-  const int z = blockIdx.y, y0 = blockIdx.x * TY;
+__device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float2* __restrict__ S,
+                                       const float2* __restrict__ twP, const Dims& d, int TY, int fwd, int z,
+                                       int y0) {
   if constexpr (HALF == 0) {
+    float kmax = 0.f;
     for (int r = threadIdx.x; r < TY; r += blockDim.x) {
       const int y = y0 + r;
       if (y >= d.ny) continue;
@@ -382,12 +396,18 @@ __global__ void __launch_bounds__(512) k_x(StageArgs a, Phys ph, float2* __restr
       float2* s1 = S + ((long long)1 * d.nz + z) * d.ny + y;
       float2* s2 = S + ((long long)2 * d.nz + z) * d.ny + y;
       const float3 bd = make_float3(ph.c_d * s0->x, ph.c_d * s1->x, ph.c_d * s2->x);
-      const float3 nm = cell_update(a, ph, d, 0, y, z, bd);
+      float km = 0.f;
+      const float3 nm = cell_update(a, ph, d, 0, y, z, bd, a.maxdmdt ? &km : nullptr);
+      kmax = fmaxf(kmax, km);
       if (fwd) {
         *s0 = make_float2(nm.x, 0.f);
         *s1 = make_float2(nm.y, 0.f);
         *s2 = make_float2(nm.z, 0.f);
       }
+    }
+    if (a.maxdmdt) {
+      const unsigned v = __reduce_max_sync(0xffffffffu, __float_as_uint(kmax));
+      if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned*>(a.maxdmdt), v);
     }
   } else {
     constexpr int T = TeamOf<HALF>::v;
@@ -434,6 +454,7 @@ __global__ void __launch_bounds__(512) k_x(StageArgs a, Phys ph, float2* __restr
     const unsigned mask = team_mask<T>(lane);
     for (int rr = team; rr < NR; rr += nteams) team_fft<HALF, T, 1, 2, PADS>(rows + rr * RS, t, mask, tws);
     __syncthreads();
+    float kmax = 0.f;
     for (int i = threadIdx.x; i < TY * d.nx; i += blockDim.x) {
       const int r = i / d.nx, x = i % d.nx;
       const int y = y0 + r;
@@ -442,8 +463,14 @@ __global__ void __launch_bounds__(512) k_x(StageArgs a, Phys ph, float2* __restr
       float& f1 = rowf<PADS>(rows + (1 * TY + r) * RS, x);
       float& f2 = rowf<PADS>(rows + (2 * TY + r) * RS, x);
       const float3 bd = make_float3(ph.c_d * f0, ph.c_d * f1, ph.c_d * f2);
-      const float3 nm = cell_update(a, ph, d, x, y, z, bd);
+      float km = 0.f;
+      const float3 nm = cell_update(a, ph, d, x, y, z, bd, a.maxdmdt ? &km : nullptr);
+      kmax = fmaxf(kmax, km);
       if (fwd) { f0 = nm.x; f1 = nm.y; f2 = nm.z; }
+    }
+    if (a.maxdmdt) {   // max |dm/dt| of the tile (non-negative floats order like their bit patterns)
+      const unsigned v = __reduce_max_sync(0xffffffffu, __float_as_uint(kmax));
+      if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned*>(a.maxdmdt), v);
     }
     if (!fwd) return;
     __syncthreads();
@@ -489,6 +516,12 @@ __global__ void __launch_bounds__(512) k_x(StageArgs a, Phys ph, float2* __restr
       if (y < d.ny) S[(((long long)k * 3 + c) * d.nz + z) * d.ny + y] = rows[(c * TY + r) * RS + pidx<PADS>(k)];
     }
   }
+}
+
+template <int HALF>
+__global__ void __launch_bounds__(512) k_x(StageArgs a, Phys ph, float2* __restrict__ S,
+                                           const float2* __restrict__ twP, Dims d, int TY, int fwd) {
+  body_x<HALF>(a, ph, S, twP, d, TY, fwd, blockIdx.y, blockIdx.x * TY);
 }
 
 // ---------------------------------------------------------------------------
@@ -704,3 +737,138 @@ int launch_normalise(const Dims& d, float* m, int* flag, cudaStream_t s) {
   k_normalise<<<(unsigned)((d.N + 255) / 256), 256, 0, s>>>(m, d.N, flag);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
+
+// ---------------------------------------------------------------------------
+// Batched launches: CTA i works on film map[i].x, tile map[i].y.  All films of
+// a launch share the padded sizes (the template parameters); their other sizes,
+// buffers and parameters come from the BatchFilm array.
+// ---------------------------------------------------------------------------
+template <int HALF>
+__global__ void __launch_bounds__(512) kb_xfwd(const BatchFilm* __restrict__ F, const int2* __restrict__ map,
+                                               int TY) {
+  const int2 ft = map[blockIdx.x];
+  const BatchFilm& f = F[ft.x];
+  if (!f.active) return;
+  const int ntyl = (f.d.ny + TY - 1) / TY;
+  const int c = ft.y / (f.d.nz * ntyl), rem = ft.y % (f.d.nz * ntyl);
+  constexpr int P = HALF == 0 ? 1 : 2 * HALF;
+  body_xfwd<HALF>(f.m0, f.S, f.tw + P, f.d, TY, c, rem / ntyl, (rem % ntyl) * TY);
+}
+
+template <int PY, int NZM>
+__global__ void __launch_bounds__(512, 1) kb_yz(const BatchFilm* __restrict__ F, const int2* __restrict__ map,
+                                                 int* flag) {
+  const int2 ft = map[blockIdx.x];
+  const BatchFilm& f = F[ft.x];
+  if (!f.active) return;
+  body_yz<PY, NZM>(f.S, f.Kh, f.tw + PY, f.d, flag, ft.y);
+}
+
+template <int HALF>
+__global__ void __launch_bounds__(512) kb_x(const BatchFilm* __restrict__ F, const int2* __restrict__ map, int TY,
+                                            int stage, float dt) {
+  const int2 ft = map[blockIdx.x];
+  const BatchFilm& f = F[ft.x];
+  if (!f.active) return;
+  const int ntyl = (f.d.ny + TY - 1) / TY;
+  StageArgs a = {};
+  a.mode = 1;
+  a.stage = stage;
+  a.dt = dt;
+  a.m0 = f.m0;
+  a.acc = f.acc;
+  a.hmap = f.hmap;
+  a.kumap = f.kumap;
+  a.m_in = stage == 0 ? f.m0 : (stage == 2 ? f.stB : f.stA);
+  a.m_out = stage == 0 ? f.stA : (stage == 1 ? f.stB : (stage == 2 ? f.stA : f.m0));
+  a.maxdmdt = stage == 0 ? f.maxdmdt : nullptr;
+  constexpr int P = HALF == 0 ? 1 : 2 * HALF;
+  body_x<HALF>(a, f.ph, f.S, f.tw + P, f.d, TY, 1, ft.y / ntyl, (ft.y % ntyl) * TY);
+}
+
+int x_batch_tile(int px, int kind) {
+  const int half = px == 1 ? 0 : px / 2;
+  if (kind == 0) return half == 0 ? 32 : xtile(half);
+  return half == 0 ? 32 : x_tile(half);
+}
+
+template <int HALF>
+static cudaError_t run_bx(const BatchFilm* F, const int2* map, int nblocks, int kind, int stage, float dt,
+                          cudaStream_t s) {
+  const int T = HALF == 0 ? 1 : TeamOf<(HALF > 0 ? HALF : 1)>::v;
+  if (kind == 0) {
+    const int TY = HALF == 0 ? 32 : xtile(HALF);
+    int threads = HALF == 0 ? 32 : TY * T;
+    threads = threads < 32 ? 32 : (threads > 512 ? 512 : threads);
+    const size_t smem = HALF == 0 ? 0 : sizeof(float2) * ((size_t)2 * HALF + (size_t)TY * (HALF + 1));
+    static bool attr = false;
+    if (cudaError_t e = allow_max_smem(kb_xfwd<HALF>, attr)) return e;
+    kb_xfwd<HALF><<<nblocks, threads, smem, s>>>(F, map, TY);
+  } else {
+    const int TY = HALF == 0 ? 32 : x_tile(HALF);
+    int threads = HALF == 0 ? 32 : ((3 * TY + 1) / 2) * T;
+    threads = (threads + 31) / 32 * 32;
+    threads = threads < 128 ? 128 : (threads > 512 ? 512 : threads);
+    static bool attr = false;
+    if (cudaError_t e = allow_max_smem(kb_x<HALF>, attr)) return e;
+    kb_x<HALF><<<nblocks, threads, x_smem(HALF), s>>>(F, map, TY, stage, dt);
+  }
+  return cudaGetLastError();
+}
+
+template <int PY, int NZM>
+static cudaError_t run_byz_t(const BatchFilm* F, const int2* map, int nblocks, size_t smem, int* flag,
+                             cudaStream_t s) {
+  static bool attr = false;
+  if (cudaError_t e = allow_max_smem(kb_yz<PY, NZM>, attr)) return e;
+  kb_yz<PY, NZM><<<nblocks, 512, smem, s>>>(F, map, flag);
+  return cudaGetLastError();
+}
+
+template <int PY>
+static cudaError_t run_byz(const BatchFilm* F, const int2* map, int nblocks, size_t smem, int nzm, int* flag,
+                           cudaStream_t s) {
+#define MM_CALL_BYZ(Z) run_byz_t<PY, Z>(F, map, nblocks, smem, flag, s)
+  MM_NZ_SWITCH(nzm, MM_CALL_BYZ)
+#undef MM_CALL_BYZ
+}
+
+int launch_batch(const BatchFilm* F, int px, int py, int nzm, const int2* map, int nblocks, size_t smem_yz,
+                 int kind, int stage, float dt, int* flag, cudaStream_t s) {
+  if (nblocks <= 0) return 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (kind == 1) {
+    switch (py) {
+      case 1: e = run_byz<1>(F, map, nblocks, smem_yz, nzm, flag, s); break;
+      case 4: e = run_byz<4>(F, map, nblocks, smem_yz, nzm, flag, s); break;
+      case 8: e = run_byz<8>(F, map, nblocks, smem_yz, nzm, flag, s); break;
+      case 16: e = run_byz<16>(F, map, nblocks, smem_yz, nzm, flag, s); break;
+      case 32: e = run_byz<32>(F, map, nblocks, smem_yz, nzm, flag, s); break;
+      case 64: e = run_byz<64>(F, map, nblocks, smem_yz, nzm, flag, s); break;
+      case 128: e = run_byz<128>(F, map, nblocks, smem_yz, nzm, flag, s); break;
+      case 256: e = run_byz<256>(F, map, nblocks, smem_yz, nzm, flag, s); break;
+      case 512: e = run_byz<512>(F, map, nblocks, smem_yz, nzm, flag, s); break;
+      case 1024: e = run_byz<1024>(F, map, nblocks, smem_yz, nzm, flag, s); break;
+      case 2048: e = run_byz<2048>(F, map, nblocks, smem_yz, nzm, flag, s); break;
+    }
+  } else {
+    const int k = kind;
+    auto go = [&](auto half_tag) { return run_bx<decltype(half_tag)::value>(F, map, nblocks, k, stage, dt, s); };
+    switch (px == 1 ? 0 : px / 2) {
+      case 0: e = go(std::integral_constant<int, 0>()); break;
+      case 2: e = go(std::integral_constant<int, 2>()); break;
+      case 4: e = go(std::integral_constant<int, 4>()); break;
+      case 8: e = go(std::integral_constant<int, 8>()); break;
+      case 16: e = go(std::integral_constant<int, 16>()); break;
+      case 32: e = go(std::integral_constant<int, 32>()); break;
+      case 64: e = go(std::integral_constant<int, 64>()); break;
+      case 128: e = go(std::integral_constant<int, 128>()); break;
+      case 256: e = go(std::integral_constant<int, 256>()); break;
+      case 512: e = go(std::integral_constant<int, 512>()); break;
+      case 1024: e = go(std::integral_constant<int, 1024>()); break;
+    }
+  }
+  return e == cudaSuccess ? 1 : -1;
+}
+
+size_t mm_yz_smem(const Dims& d) { return yz_smem(d); }

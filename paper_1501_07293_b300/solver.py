@@ -59,6 +59,15 @@ _SIGNATURES = {
     "mm_heff_noalloc": (_I, [ctypes.POINTER(_I), _D, _D, _D, _D, ctypes.POINTER(_D), _I, _P, _P,
                              ctypes.c_uint, _P]),
     "mm_noalloc_last_error": (ctypes.c_char_p, []),
+    "mm_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), _D, _D, _D, _D, _D, _D, ctypes.POINTER(Opts)]),
+    "mm_batch_destroy": (None, [_P]),
+    "mm_batch_film": (_P, [_P, _I]),
+    "mm_batch_step": (_I, [_P, _I, _D]),
+    "mm_batch_run": (_I, [_P, _I, _D, _D, _I, ctypes.POINTER(_I)]),
+    "mm_batch_max_dmdt": (_I, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "mm_batch_group_count": (_I, [_P]),
+    "mm_batch_launch_count": (ctypes.c_longlong, [_P]),
+    "mm_batch_last_error": (ctypes.c_char_p, [_P]),
 }
 
 _lib = None
@@ -241,3 +250,82 @@ def heff_noalloc(grid, delta, Ms, A, Ku, b_ext, m, H, mask: int = TERM_ALL, self
     if rc != MM_OK:
         raise MMError(rc, L.mm_noalloc_last_error().decode())
     return H
+
+
+class _FilmView(Solver):
+    """A film of a Batch: the single-film API on the batch-owned context (not destroyed here)."""
+
+    def __init__(self, batch, index, ctx, grid):
+        self.torch = batch.torch
+        self.device = batch.device
+        self.grid = tuple(grid)
+        self.N = grid[0] * grid[1] * grid[2]
+        self.ctx = ctx
+        self._L = batch._L
+        self._stream = batch._stream
+
+    def close(self):
+        self.ctx = None
+
+
+class Batch:
+    """Independent films of uneven size advanced together (mm_batch_*)."""
+
+    def __init__(self, grids, delta, Ms, A, Ku, alpha, gamma, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.grids = [tuple(int(v) for v in g) for g in grids]
+        L = lib()
+        o = Opts()
+        L.mm_default_opts(ctypes.byref(o))
+        with torch.cuda.device(self.device):
+            s = torch.cuda.current_stream() if stream is None else stream
+            o.stream = s.cuda_stream
+            self._stream = s
+            flat = (_I * (3 * len(self.grids)))(*[v for g in self.grids for v in g])
+            b = _P()
+            rc = L.mm_batch_create(ctypes.byref(b), len(self.grids), flat, float(delta), float(Ms), float(A),
+                                   float(Ku), float(alpha), float(gamma), ctypes.byref(o))
+            if rc != MM_OK:
+                raise MMError(rc, L.mm_batch_last_error(None).decode())
+        self.b = b
+        self._L = L
+        self.films = [_FilmView(self, f, L.mm_batch_film(b, f), g) for f, g in enumerate(self.grids)]
+
+    def _check(self, rc):
+        if rc != MM_OK:
+            raise MMError(rc, self._L.mm_batch_last_error(self.b).decode())
+
+    def step(self, n: int, dt: float):
+        self._check(self._L.mm_batch_step(self.b, int(n), float(dt)))
+
+    def run(self, max_steps: int, dt: float, tol_dmdt: float, check_every: int = 100):
+        out = (_I * len(self.grids))()
+        self._check(self._L.mm_batch_run(self.b, int(max_steps), float(dt), float(tol_dmdt), int(check_every), out))
+        return list(out)
+
+    def max_dmdt(self):
+        out = (ctypes.c_float * len(self.grids))()
+        self._check(self._L.mm_batch_max_dmdt(self.b, out))
+        return np.array(out[:], dtype=np.float64)
+
+    def group_count(self) -> int:
+        return int(self._L.mm_batch_group_count(self.b))
+
+    def launch_count(self) -> int:
+        return int(self._L.mm_batch_launch_count(self.b))
+
+    def close(self):
+        if getattr(self, "b", None):
+            for f in self.films:
+                f.close()
+            self._L.mm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
