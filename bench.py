@@ -43,6 +43,7 @@ def parse_args():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="film_256x256x16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched-sweep and adjoint measurements")
     ap.add_argument("--ref-max-steps", type=int, default=8,
                     help="reference arm: at most this many oracle RK4 steps are executed and timed")
     return ap.parse_args()
@@ -202,6 +203,73 @@ def reference_arm(args, w):
 # ---------------------------------------------------------------------------
 # B300 arm
 # ---------------------------------------------------------------------------
+def bench_batched(args, steps=40, warmup=5):
+    """The field-sweep workload: 256 independent films of uneven size, RK4, one batch."""
+    import torch
+    from paper_1501_07293_b300 import inputs
+    from paper_1501_07293_b300.solver import Batch
+    films = inputs.film_batch()
+    mat = inputs.BATCH_MATERIAL
+    b = Batch([f.grid for f in films], inputs.BATCH_DELTA, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma)
+    for f in films:
+        b.films[f.index].set_field(f.b_ext)
+        b.films[f.index].set_m(torch.from_numpy(inputs.initial_state("tilted_x", f.grid, f.seed)).cuda())
+    b.step(warmup, inputs.BATCH_DT)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = b.launch_count()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(steps, inputs.BATCH_DT)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    cells = sum(g[0] * g[1] * g[2] for g in b.grids)
+    out = {"workload": "256 films, nx 32..256, ny 8..128, nz 1..4, fields -50..50 mT, RK4 dt 1e-13 s",
+           "value": cells * steps / (ms * 1e-3), "unit": UNIT, "cells": cells, "steps": steps,
+           "ms_per_step": ms / steps, "groups": b.group_count(), "gpu_launches": b.launch_count() - l0,
+           "l2": "working set larger than L2 (no flush)"}
+    b.close()
+    return out
+
+
+def bench_adjoint(args, reps=3):
+    """Differentiation study: 128x128x4 film, 500 RK4 steps, checkpoint every 50; adjoint / forward time."""
+    import torch
+    from paper_1501_07293_b300 import inputs
+    from paper_1501_07293_b300.solver import Solver
+    w = inputs.film_128x128x4()
+    mat = w.mat
+    s = Solver(w.grid, w.delta, mat.Ms, mat.A, 0.0, mat.alpha, mat.gamma)
+    h = torch.from_numpy(inputs.zeeman_map(w.grid, 5001)).cuda()
+    ku = torch.from_numpy(inputs.ku_map(w.grid, 5002)).cuda()
+    s.set_field((0.0, 0.0, 0.0), h, ku)
+    m0 = torch.from_numpy(inputs.workload_state(w)).cuda()
+    g = torch.full_like(m0, 1e-5)
+    stream = torch.cuda.current_stream()
+    fwd, adj = [], []
+    for r in range(reps + 1):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        s.set_m(m0)
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        s.step(w.steps, w.dt)
+        e[1].record(stream)
+        s.set_m(m0)
+        e[2].record(stream)
+        s.adjoint(w.steps, w.dt, 50, g)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        if r:   # first round warms up (graph capture, workspace allocation)
+            fwd.append(e[0].elapsed_time(e[1]))
+            adj.append(e[2].elapsed_time(e[3]))
+    s.close()
+    f, a = statistics.median(fwd), statistics.median(adj)
+    return {"workload": "film_128x128x4, 500 RK4 steps, checkpoint every 50, gradients w.r.t. m0, h, Ku",
+            "forward_ms": f, "adjoint_ms": a, "adjoint_over_forward": a / f,
+            "note": "adjoint time includes its own forward pass with checkpoints and one recomputation"}
+
+
 def b300_arm(args, w):
     import torch
     import torch.distributed as dist
@@ -297,6 +365,11 @@ def b300_arm(args, w):
     e2e = world * w.ncells * Ke / t_e2e
     nbytes = 3 * w.ncells * 4
 
+    extra = {}
+    if not args.no_extras:
+        extra["batched"] = bench_batched(args)
+        extra["adjoint"] = bench_adjoint(args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, cores, wall, n = time_oracle(w, 1, 0)
@@ -324,6 +397,7 @@ def b300_arm(args, w):
                     "path": "mm_set_m(pinned host) + mm_step(1) + mm_get_m(pinned host)"},
             "gpu_launches": launches,
             "cpu_baseline": cpu,
+            **extra,
         }
         print(json.dumps(out), flush=True)
     s.close()
