@@ -6,7 +6,7 @@
 //   S                       [hx][3][nz][ny]   float2: x-transformed field
 //                                             (kx-major, so one kx column of the
 //                                             y/z pass is a contiguous slab)
-//   Kh                      [hx][6][nz][hy]   demag kernel transformed along x
+//   Kh                      [hx][hy][6][nz]   demag kernel transformed along x
 //                                             and y, real space along z
 //                                             (pairs xx yy zz xy xz yz)
 //   tw                      [2 Lmax]          float2 twiddles; the table of

@@ -116,14 +116,25 @@ __device__ __forceinline__ void zprod(int a, const float2* __restrict__ buf, int
     const bool odd_z = (p >= 4);              // xz, yz: odd in z and imaginary
     const float ys = (mirrored && odd_y) ? -1.f : 1.f;
     const float zs = odd_z ? -ys : ys;
-    const float* kp = Kk + (long long)p * nz * hy + kyf;
+    const float* kp = Kk + ((long long)kyf * 6 + p) * nz;   // the nz offsets of this pair, contiguous
     float kr[NZM], kn[NZM];   // kernel at offsets +q and -q
     float2 mv[NZM];
+    if (NZM % 4 == 0 && (nz & 3) == 0) {
 #pragma unroll
-    for (int q = 0; q < NZM; ++q) {
-      const float v = (q < nz) ? __ldg(kp + (long long)q * hy) : 0.f;
-      kr[q] = ys * v;
-      kn[q] = zs * v;
+      for (int q4 = 0; q4 < NZM / 4; ++q4) {
+        const float4 v = (4 * q4 < nz) ? __ldg(reinterpret_cast<const float4*>(kp) + q4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        kr[4 * q4 + 0] = ys * v.x; kn[4 * q4 + 0] = zs * v.x;
+        kr[4 * q4 + 1] = ys * v.y; kn[4 * q4 + 1] = zs * v.y;
+        kr[4 * q4 + 2] = ys * v.z; kn[4 * q4 + 2] = zs * v.z;
+        kr[4 * q4 + 3] = ys * v.w; kn[4 * q4 + 3] = zs * v.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < NZM; ++q) {
+        const float v = (q < nz) ? __ldg(kp + q) : 0.f;
+        kr[q] = ys * v;
+        kn[q] = zs * v;
+      }
     }
 #pragma unroll
     for (int zi = 0; zi < NZM; ++zi) {
@@ -242,7 +253,7 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   }
   // Product of eq. 14 along z (see zprod).
   if (PY > 1)
-    zprod_column<NZM, PADS>(buf, RS, PY, nz, Kh + (long long)kx * 6 * nz * d.hy, d.hy, PY, KyIdentity());
+    zprod_column<NZM, PADS>(buf, RS, PY, nz, Kh + (long long)kx * d.hy * 6 * nz, d.hy, PY, KyIdentity());
   else
     zprod_column<NZM, 0>(buf, RS, PY, nz, Kh + (long long)kx * 6 * nz * d.hy, d.hy, PY, KyIdentity());
   __syncthreads();

@@ -9,7 +9,7 @@
 // 2. k_fft64: FP64 radix-2 Stockham transforms along x, then y, of every plane
 //    (the convolution theorem of eq. 14 along x and y; z stays in real space).
 // 3. k_extract: keeps kx in [0, px/2], ky in [0, py/2] (the rest follows from
-//    the tensor's parity) and stores float32 Kh[kx][pair][K][ky].  Pairs xx, yy,
+//    the tensor's parity) and stores float32 Kh[kx][ky][pair][K].  Pairs xx, yy,
 //    zz, xy transform to real numbers, xz and yz to imaginary ones (they are odd
 //    in exactly one of x, y); the imaginary part is stored for those two.
 #include <math.h>
@@ -101,12 +101,13 @@ __global__ void k_extract(const double2* __restrict__ Kc, float* __restrict__ Kh
   const long long total = (long long)d.hx * 6 * d.nz * d.hy;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
-  const int ky = (int)(idx % d.hy);
-  long long r = idx / d.hy;
-  const int kz = (int)(r % d.nz);
-  r /= d.nz;
+  // Kh[kx][ky][pair][K]: the nz values one (kx, ky, pair) needs are contiguous
+  const int kz = (int)(idx % d.nz);
+  long long r = idx / d.nz;
   const int p = (int)(r % 6);
-  const int kx = (int)(r / 6);
+  r /= 6;
+  const int ky = (int)(r % d.hy);
+  const int kx = (int)(r / d.hy);
   const long long plane = (long long)d.px * d.py;
   const double2 v = Kc[((long long)p * d.nz + kz) * plane + (long long)ky * d.px + kx];
   Kh[idx] = (float)(p < 4 ? v.x : v.y);
