@@ -428,16 +428,19 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
     extern __shared__ float2 sm[];
     float2* tws = sm;
     float2* rows = sm + P;   // [3][TY] rows, element k at pidx(k), k <= HALF
-    for (int i = threadIdx.x; i < P; i += blockDim.x) tws[i] = twP[i];
     const int total = (HALF + 1) * 3 * TY;
+    // the tile of S arrives by asynchronous copies (all in flight at once)
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
       const int r = i % TY, rest = i / TY;
       const int c = rest % 3, k = rest / 3;
       const int y = y0 + r;
-      float2 v = make_float2(0.f, 0.f);
-      if (y < d.ny) v = S[(((long long)k * 3 + c) * d.nz + z) * d.ny + y];
-      rows[(c * TY + r) * RS + pidx<PADS>(k)] = v;
+      float2* dst = rows + (c * TY + r) * RS + pidx<PADS>(k);
+      if (y < d.ny) cp_async8(dst, S + (((long long)k * 3 + c) * d.nz + z) * d.ny + y);
+      else *dst = make_float2(0.f, 0.f);
     }
+    cp_async_commit();
+    for (int i = threadIdx.x; i < P; i += blockDim.x) tws[i] = twP[i];
+    cp_async_wait_all();
     __syncthreads();
     // Z[k] = (X[k] + conj X[HALF-k]) + i W_P^{-k} (X[k] - conj X[HALF-k]), k < HALF
     const int NR = 3 * TY;
@@ -486,14 +489,16 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
     if (!fwd) return;
     __syncthreads();
     // zero padding nx..P-1 of every valid row, then the forward half-length transform
-    for (int i = threadIdx.x; i < NR * (P - d.nx); i += blockDim.x) {
-      const int rr = i / (P - d.nx), x = d.nx + i % (P - d.nx);
-      rowf<PADS>(rows + rr * RS, x) = 0.f;
+    // zero padding nx..P-1: the first pass reads only the (nx+1)/2 packed samples;
+    // for odd nx the partner of the last sample is cleared below
+    if (d.nx & 1) {
+      for (int rr = threadIdx.x; rr < NR; rr += blockDim.x) rowf<PADS>(rows + rr * RS, d.nx) = 0.f;
     }
     __syncthreads();
+    const int nin = (d.nx + 1) / 2;
     for (int rr = team; rr < NR; rr += nteams) {
       if (y0 + rr % TY >= d.ny) continue;
-      team_fft<HALF, T, -1, 2, PADS>(rows + rr * RS, t, mask, tws);
+      team_fft_io<HALF, T, -1, 2, PADS, PADS, PADS>(rows + rr * RS, t, mask, tws, nin, HALF);
     }
     __syncthreads();
     // X[k] = 1/2 (Z[k] + conj Z[-k]) - i/2 W_P^k (Z[k] - conj Z[-k]), in place by pairs (k, HALF-k)
