@@ -388,6 +388,12 @@ __device__ __forceinline__ float3 cell_update(const StageArgs& a, const Phys& ph
 // state just written, stored back into the same tile of S for the next field
 // evaluation (so a stage needs only k_yz2 + k_x).
 // ---------------------------------------------------------------------------
+// Rows per tile of the x kernels.
+template <int HALF>
+struct XTile {
+  static constexpr int v = HALF <= 256 ? 8 : (HALF <= 512 ? 4 : 2);
+};
+
 template <int PADS>
 __device__ __forceinline__ float& rowf(float2* row, int x) {
   float2& e = row[pidx<PADS>(x >> 1)];
@@ -425,6 +431,7 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
     constexpr int P = 2 * HALF;
     constexpr int PADS = 4;
     constexpr int RS = HALF + (HALF + 1) / 16 + 2;
+    constexpr int TY = XTile<HALF>::v;   // rows per tile (the launcher uses the same value)
     extern __shared__ float2 sm[];
     float2* tws = sm;
     float2* rows = sm + P;   // [3][TY] rows, element k at pidx(k), k <= HALF
@@ -469,8 +476,9 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
     for (int rr = team; rr < NR; rr += nteams) team_fft<HALF, T, 1, 2, PADS>(rows + rr * RS, t, mask, tws);
     __syncthreads();
     float kmax = 0.f;
-    for (int i = threadIdx.x; i < TY * d.nx; i += blockDim.x) {
-      const int r = i / d.nx, x = i % d.nx;
+    for (int i = threadIdx.x; i < TY * HALF; i += blockDim.x) {
+      const int r = i / HALF, x = i % HALF;   // nx <= HALF
+      if (x >= d.nx) continue;
       const int y = y0 + r;
       if (y >= d.ny) continue;
       float& f0 = rowf<PADS>(rows + (0 * TY + r) * RS, x);
