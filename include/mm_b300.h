@@ -187,6 +187,16 @@ int mm_adjoint(mm_ctx* ctx, int n, double dt, int ckpt_every, const float* dL_dm
 /* Number of kernels this context has enqueued so far (graph nodes counted per replay). */
 long long mm_launch_count(const mm_ctx* ctx);
 
+/*
+ * Self-test of the failure path of the kernels' bounded waits (the paper has
+ * no counterpart): enqueues one CTA that polls an mbarrier phase nothing
+ * completes, gives up after `polls` (1 .. 2^20) polls, sets the timeout flag
+ * and returns, as a kernel whose bulk copy never lands would.  The next
+ * mm_sync / mm_energy / mm_observables returns MM_ETIMEOUT and clears the flag;
+ * the context stays usable.
+ */
+int mm_selftest_wait_timeout(mm_ctx* ctx, unsigned polls);
+
 /* Block until the context's stream is idle; reports a pending device-side error. */
 int mm_sync(mm_ctx* ctx);
 

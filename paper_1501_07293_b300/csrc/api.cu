@@ -497,3 +497,35 @@ extern "C" int mm_sync(mm_ctx* c) {
 }
 
 extern "C" const char* mm_last_error(const mm_ctx* c) { return c ? c->err : g_create_err; }
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded device waits: one CTA waits on an mbarrier phase that
+// nothing completes, gives up after `polls` polls, sets the context's timeout
+// flag and returns; mm_sync then reports MM_ETIMEOUT.  No fault, no trap, no hang.
+// ---------------------------------------------------------------------------
+__global__ void k_wait_selftest(int* flag, unsigned polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(&bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(1) : "memory");
+  for (unsigned i = 0; i < polls; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(0u)
+        : "memory");
+    if (ok) return;   // never: no thread arrives on the barrier
+  }
+  atomicOr(flag + 1, 1);
+}
+
+extern "C" int mm_selftest_wait_timeout(mm_ctx* c, unsigned polls) {
+  if (!c) return MM_EINVAL;
+  if (polls < 1 || polls > (1u << 20)) return mm_fail(c, MM_EINVAL, "mm_selftest_wait_timeout: polls out of range");
+  k_wait_selftest<<<1, 32, 0, c->stream>>>(c->dflag, polls);
+  if (cudaGetLastError() != cudaSuccess) return mm_fail(c, MM_ECUDA, "self-test launch failed");
+  c->launches++;
+  return MM_OK;
+}

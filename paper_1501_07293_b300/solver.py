@@ -55,6 +55,7 @@ _SIGNATURES = {
     "mm_adjoint": (_I, [_P, _I, _D, _I, _P, _P, _P, _P]),
     "mm_launch_count": (ctypes.c_longlong, [_P]),
     "mm_sync": (_I, [_P]),
+    "mm_selftest_wait_timeout": (_I, [_P, ctypes.c_uint]),
     "mm_last_error": (ctypes.c_char_p, [_P]),
     "mm_heff_noalloc": (_I, [ctypes.POINTER(_I), _D, _D, _D, _D, ctypes.POINTER(_D), _I, _P, _P,
                              ctypes.c_uint, _P]),
@@ -230,6 +231,10 @@ class Solver:
 
     def sync(self):
         self._check(self._L.mm_sync(self.ctx))
+
+    def selftest_wait_timeout(self, polls: int = 1000):
+        """Enqueue a kernel whose bounded wait runs out (see mm_selftest_wait_timeout)."""
+        self._check(self._L.mm_selftest_wait_timeout(self.ctx, int(polls)))
 
 
 def heff_noalloc(grid, delta, Ms, A, Ku, b_ext, m, H, mask: int = TERM_ALL, self_term: bool = True,

@@ -136,3 +136,23 @@ def test_nonfinite_state_is_reported():
         s.sync()
     assert e.value.code == MM_ENONFINITE
     s.close()
+
+
+def test_bounded_wait_timeout_is_reported_and_recoverable():
+    # a kernel whose wait runs out sets the flag; the host sees MM_ETIMEOUT, the context keeps working
+    import torch
+    from paper_1501_07293_b300.solver import MM_ETIMEOUT, MMError
+    from oracle.llg import TERM_ALL
+    grid = (16, 8, 2)
+    m = inputs.random_state(grid, 4)
+    s = make_solver(grid, 4e-9)
+    s.set_m(torch.from_numpy(m).cuda())
+    s.selftest_wait_timeout(2000)
+    with pytest.raises(MMError) as e:
+        s.sync()
+    assert e.value.code == MM_ETIMEOUT
+    s.sync()   # flag cleared
+    Hg = gpu_heff(s, m, TERM_ALL)
+    Ho = to_device(make_film(grid, 4e-9).h_eff(to_xyz(m), TERM_ALL))
+    assert rel_l2(Hg, Ho) <= TOL
+    s.close()
