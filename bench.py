@@ -270,6 +270,48 @@ def bench_adjoint(args, reps=3):
             "note": "adjoint time includes its own forward pass with checkpoints and one recomputation"}
 
 
+def bench_sp4(args, sample_every=1000):
+    """The paper's validation run: standard problem 4 on 166x42x1 cells of 3 nm in
+    the paper's mode (explicit Euler at dt = 5 fs, tensor without the self offset),
+    the full 150,000-step protocol as a device field program, <m> every 1000 steps."""
+    import torch
+    from paper_1501_07293_b300 import inputs
+    from paper_1501_07293_b300.solver import Solver
+    w = inputs.sp4_film()
+    mat = w.mat
+    s = Solver(w.grid, w.delta, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma, integrator="euler",
+               self_term=False)
+    s.set_m(torch.from_numpy(inputs.workload_state(w)).cuda())
+    s.set_program(inputs.sp4_schedule(w.dt))
+    s.step(1, w.dt)   # graph capture
+    s.set_m(torch.from_numpy(inputs.workload_state(w)).cuda())
+    s.set_time(0.0)
+    stream = torch.cuda.current_stream()
+    chunks = w.steps // sample_every
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(chunks)]
+    means = []
+    l0 = s.launch_count()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(chunks):
+        ev[k][0].record(stream)
+        s.step(sample_every, w.dt)
+        ev[k][1].record(stream)
+        means.append(s.observables()[:3].tolist())
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    out = {"workload": "muMAG standard problem 4 protocol, 166x42x1 cells of 3 nm, Euler dt 5 fs, "
+                       "150,000 steps, self offset skipped (paper mode)",
+           "steps": w.steps, "ms_per_step": step_ms / w.steps, "wall_s_with_sampling": wall,
+           "value": w.ncells * w.steps / (step_ms * 1e-3), "unit": UNIT,
+           "gpu_launches": s.launch_count() - l0,
+           "mean_m_at_50000_steps": means[50000 // sample_every - 1],
+           "mean_m_final": means[-1]}
+    s.close()
+    return out
+
+
 def b300_arm(args, w):
     import torch
     import torch.distributed as dist
@@ -369,6 +411,7 @@ def b300_arm(args, w):
     if not args.no_extras:
         extra["batched"] = bench_batched(args)
         extra["adjoint"] = bench_adjoint(args)
+        extra["sp4_protocol"] = bench_sp4(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -109,12 +109,54 @@ int mm_get_m(mm_ctx* ctx, float* m);
  * Applied field: b_ext = mu0 H_ext (tesla, 3 doubles, host).  h_map (host or
  * device, [3][nz][ny][nx] tesla) is an optional per-cell addition, ku_map
  * (host or device, [nz][ny][nx] J/m^3) an optional per-cell Ku that replaces
- * the scalar Ku.  NULL clears a map.  The maps are copied.
+ * the scalar Ku.  NULL clears a map.  The maps are copied.  The next mm_step
+ * patches the new values into its captured step graph in place (re-capture +
+ * graph update, no re-instantiation), so a host loop of mm_set_field +
+ * mm_step (a hysteresis sweep) stays cheap.
  */
 int mm_set_field(mm_ctx* ctx, const double b_ext[3], const float* h_map, const float* ku_map);
 
-/* Change the damping constant (the paper switches alpha between its relax and reverse phases). */
+/* Change the damping constant (the paper switches alpha between its relax and
+ * reverse phases).  Patched into the step graph like b_ext. */
 int mm_set_alpha(mm_ctx* ctx, double alpha);
+
+/*
+ * Field program: a time-dependent uniform field and damping evaluated on the
+ * device at every stage of every step, so that a whole protocol such as the
+ * paper's standard-problem-4 run (saturate along (1,1,1), ramp down, then
+ * reverse with a damping switch; Section 3 and the script of Appendix A) runs
+ * as graph replays without host round trips.
+ *
+ * Each context has a clock (seconds, FP64, on the device): mm_step advances it
+ * by dt per step, and the RK4 stages of the step from t evaluate the program
+ * at t, t + dt/2, t + dt/2, t + dt (Euler at t).  At time t the first segment
+ * with t_begin <= t < t_end gives
+ *     b_ext(t) = b_begin + (t - t_begin) / (t_end - t_begin) (b_end - b_begin),
+ *     alpha(t) = alpha (segment value; alpha < 0 keeps the context's alpha);
+ * outside every segment the context's b_ext / alpha (mm_set_field, mm_set_alpha)
+ * apply.  mm_heff, mm_energy and mm_observables use the values at the clock.
+ */
+#define MM_PROGRAM_MAX 32
+typedef struct {
+  double t_begin, t_end;   /* seconds, t_end > t_begin                          */
+  double b_begin[3];       /* mu0 H_ext at t_begin, tesla                       */
+  double b_end[3];         /* mu0 H_ext approached at t_end, tesla              */
+  double alpha;            /* damping inside the segment; < 0: context's alpha  */
+} mm_segment;
+
+/* Install nseg (0 .. MM_PROGRAM_MAX) segments (host array, copied; nseg 0
+ * removes the program).  Stream-ordered.  MM_EINVAL for a non-finite value or
+ * t_end <= t_begin.  While a program is installed the field and damping are
+ * read from device memory at every stage, so changing the segments, b_ext or
+ * alpha needs no graph update at all. */
+int mm_set_program(mm_ctx* ctx, int nseg, const mm_segment* seg);
+
+/* Set the clock (stream-ordered).  mm_create starts it at 0; mm_set_m does not
+ * change it. */
+int mm_set_time(mm_ctx* ctx, double t);
+
+/* Read the clock into *t (host).  Synchronises. */
+int mm_get_time(mm_ctx* ctx, double* t);
 
 /*
  * Effective field (eq. 3) of the current state, restricted to the terms in
@@ -179,7 +221,8 @@ int mm_step_timed(mm_ctx* ctx, int n, double dt, double ms_out[3]);
  * one recomputed segment (8 ckpt_every + 1 vector fields), allocated on the
  * first call and kept.  Cost: one forward pass, one recomputation, and four
  * applications of the symmetric exchange + demag operator per step.  RK4 only
- * (MM_EUNSUPPORTED for Euler).  Asynchronous.
+ * (MM_EUNSUPPORTED for Euler or while a field program is installed: the
+ * derivative assumes a constant uniform field and damping).  Asynchronous.
  */
 int mm_adjoint(mm_ctx* ctx, int n, double dt, int ckpt_every, const float* dL_dm_final,
                float* dL_dh, float* dL_dku, float* dL_dm0);

@@ -162,6 +162,8 @@ extern "C" int mm_adjoint(mm_ctx* c, int n, double dt, int ckpt_every, const flo
   if (!(dt > 0) || dt > 1e-6) return mm_fail(c, MM_EINVAL, "mm_adjoint: dt = %g s out of range", dt);
   if (!dL_dm_final) return mm_fail(c, MM_EINVAL, "mm_adjoint: dL_dm_final is NULL");
   if (c->opts.integrator != MM_RK4) return mm_fail(c, MM_EUNSUPPORTED, "mm_adjoint: only the RK4 integrator");
+  if (c->prog_n > 0)
+    return mm_fail(c, MM_EUNSUPPORTED, "mm_adjoint: a field program is installed (constant field and damping only)");
   const long long N = c->d.N;
   const size_t v3 = 3 * (size_t)N;
   const int k = ckpt_every < n ? ckpt_every : n;

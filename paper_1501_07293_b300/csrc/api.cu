@@ -64,7 +64,7 @@ static void free_ctx(mm_ctx* c) {
   drop_graphs(c);
   cudaFree(c->m0); cudaFree(c->stA); cudaFree(c->stB); cudaFree(c->acc); cudaFree(c->Hs);
   cudaFree(c->hmap); cudaFree(c->kumap); cudaFree(c->S); cudaFree(c->Kh); cudaFree(c->tw);
-  cudaFree(c->red); cudaFree(c->red_out); cudaFree(c->dflag);
+  cudaFree(c->red); cudaFree(c->red_out); cudaFree(c->dflag); cudaFree(c->prog);
   mm_adjoint_free(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->ev) cudaEventDestroy(c->ev);
@@ -141,6 +141,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double M
     ALLOC(c->red, sizeof(double) * 9 * (size_t)nb);
     ALLOC(c->red_out, sizeof(double) * 16);
     ALLOC(c->dflag, sizeof(int) * 4);
+    ALLOC(c->prog, sizeof(ProgState));
   }
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) {
@@ -150,6 +151,10 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double M
   }
   if (cudaMemsetAsync(c->dflag, 0, sizeof(int) * 4, c->stream) != cudaSuccess) {
     rc = mm_fail(nullptr, MM_ECUDA, "memset failed");
+    goto fail;
+  }
+  if (mm_prog_init(c) != MM_OK) {
+    rc = mm_fail(nullptr, MM_ECUDA, "field program initialisation failed");
     goto fail;
   }
   rc = mm_build_kernel(c);
@@ -236,24 +241,38 @@ extern "C" int mm_set_field(mm_ctx* c, const double b_ext[3], const float* h_map
     cudaFree(c->kumap);
     c->kumap = nullptr;
   }
-  drop_graphs(c);  // kernel arguments changed
-  return MM_OK;
+  c->graph_valid = 0;   // kernel parameters changed: re-captured and updated in place by mm_step
+  return mm_prog_push_base(c);
 }
 
 extern "C" int mm_set_alpha(mm_ctx* c, double alpha) {
   if (!c) return MM_EINVAL;
   if (!(alpha >= 0)) return mm_fail(c, MM_EINVAL, "alpha must be >= 0");
   c->alpha = alpha;
-  drop_graphs(c);
-  return MM_OK;
+  c->graph_valid = 0;
+  return mm_prog_push_base(c);
 }
+
+// Device address of drive slot s (0..3: RK4 stages of the step under way, 4:
+// at the clock) while a field program is installed; otherwise NULL and the
+// kernels take the uniform field and damping from their parameters.
+static const float* drive_slot(mm_ctx* c, int s) { return c->prog_n > 0 ? &c->prog->drive[s][0] : nullptr; }
 
 static StageArgs base_args(mm_ctx* c) {
   StageArgs a;
   memset(&a, 0, sizeof a);
   a.hmap = c->hmap;
   a.kumap = c->kumap;
+  a.drive = drive_slot(c, 4);
   return a;
+}
+
+// Stage s of a step: its drive slot, and at s = 0 the tick that advances the
+// clock (always) and fills the slots.
+static void stage_drive(mm_ctx* c, StageArgs& a, int s, double dt) {
+  a.drive = drive_slot(c, s);
+  a.tick = Tick{};
+  if (s == 0) a.tick = Tick{c->prog, dt, c->opts.integrator == MM_EULER};
 }
 
 extern "C" int mm_heff(mm_ctx* c, float* H, unsigned mask) {
@@ -284,6 +303,7 @@ static int enqueue_step(mm_ctx* c, cudaStream_t s, double dt, int from, long lon
     a.mode = 2;
     a.m_in = from ? c->stA : c->m0;
     a.m_out = from ? c->m0 : c->stA;
+    stage_drive(c, a, 0, dt);
     const int k = launch_stage(c->d, ph, a, c->tw, c->S, c->Kh, c->dflag, s);
     if (k < 0) return k;
     *nk += k;
@@ -298,6 +318,7 @@ static int enqueue_step(mm_ctx* c, cudaStream_t s, double dt, int from, long lon
     a.stage = s4;
     a.m_in = in[s4];
     a.m_out = outp[s4];
+    stage_drive(c, a, s4, dt);
     const int k = launch_stage(c->d, ph, a, c->tw, c->S, c->Kh, c->dflag, s);
     if (k < 0) return k;
     *nk += k;
@@ -315,8 +336,11 @@ static int ensure_spectrum(mm_ctx* c) {
   return MM_OK;
 }
 
+// Capture the step sequence.  An existing executable graph of the same shape
+// (only kernel parameters changed: dt, the field, the damping, map pointers)
+// is updated in place; otherwise it is instantiated anew.
 static int build_graphs(mm_ctx* c, double dt) {
-  drop_graphs(c);
+  if (c->graph_integrator != c->opts.integrator) drop_graphs(c);
   const int ng = c->opts.integrator == MM_EULER ? 2 : 1;
   for (int g = 0; g < ng; ++g) {
     cudaGraph_t graph;
@@ -328,9 +352,27 @@ static int build_graphs(mm_ctx* c, double dt) {
       cudaGetLastError();
       return mm_fail(c, MM_ECUDA, "graph capture failed (%d, %s)", r, cudaGetErrorString(e));
     }
-    e = cudaGraphInstantiate(&c->graph[g], graph, 0);
+    bool updated = false;
+    if (c->graph[g]) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(c->graph[g], graph, &info) == cudaSuccess) {
+        updated = true;
+      } else {
+        cudaGetLastError();
+        cudaGraphExecDestroy(c->graph[g]);
+        c->graph[g] = nullptr;
+      }
+    }
+    if (!updated) {
+      e = cudaGraphInstantiate(&c->graph[g], graph, 0);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        c->graph[g] = nullptr;
+        c->graph_valid = 0;
+        return mm_fail(c, MM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+      }
+    }
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return mm_fail(c, MM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     c->graph_nodes[g] = nk;
   }
   c->graph_valid = 1;
@@ -408,6 +450,7 @@ extern "C" int mm_step_timed(mm_ctx* c, int n, double dt, double ms_out[3]) {
       a.stage = s4;
       a.m_in = in[s4];
       a.m_out = outp[s4];
+      stage_drive(c, a, s4, dt);
       for (int part = 1; part < 3; ++part) {
         if (launch_field_part(c->d, ph, a, c->tw, c->S, c->Kh, c->dflag, c->stream, part) < 0) {
           rc = mm_fail(c, MM_ECUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -458,7 +501,7 @@ static int run_reduce(mm_ctx* c, double* host) {
   c->s_valid = 0;
   if (k < 0) return mm_fail(c, MM_ECUDA, "field kernels failed to launch");
   c->launches += k;
-  k = launch_reduce(c->d, ph, state_ptr(c), c->Hs, c->hmap, c->kumap, c->A, c->Ku, c->delta, c->Ms, c->red,
+  k = launch_reduce(c->d, ph, drive_slot(c, 4), state_ptr(c), c->Hs, c->hmap, c->kumap, c->A, c->Ku, c->delta, c->Ms, c->red,
                     c->red_blocks, c->red_out, c->dflag, c->stream);
   if (k < 0) return mm_fail(c, MM_ECUDA, "reduction kernels failed to launch");
   c->launches += k;

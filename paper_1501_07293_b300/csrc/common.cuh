@@ -40,6 +40,31 @@ struct Phys {
   float inv_mu0;   // 1/mu0 (tesla -> A/m)
 };
 
+// Field program (device memory, one per context).  Written only in stream
+// order: by single-CTA set-up kernels and, once per step, by the first warp of
+// the first y/z CTA (prog_tick), which nothing else in that kernel reads.
+struct ProgSeg {
+  double t0, t1;        // [t0, t1), seconds
+  float b0[3], b1[3];   // mu0 H_ext at t0 and approached at t1 (T), linear in between
+  float g1, g2;         // LLG prefactors inside the segment (when own_g)
+  int own_g;            // 0: the context's damping applies inside the segment
+  int pad;
+};
+struct ProgState {
+  double clock;         // context time (s) of the current state
+  int nseg, pad;
+  float base[8];        // bx, by, bz, g1, g2 outside every segment
+  float drive[5][8];    // bx, by, bz, g1, g2 at RK4 stages 0..3 of the step under way; [4] at `clock`
+  ProgSeg seg[MM_PROGRAM_MAX];
+};
+// Carried by the first y/z launch of a step: advance the clock by dt and write
+// the drive slots of the step (p null: nothing).
+struct Tick {
+  ProgState* p;
+  double dt;
+  int euler;
+};
+
 // One field evaluation / stage.  mode: 0 = write H_eff, 1 = RK4 stage, 2 = Euler step.
 struct StageArgs {
   const float* m_in;   // state the field is evaluated at (read with neighbours)
@@ -51,6 +76,8 @@ struct StageArgs {
   float* maxdmdt;      // modes 1/2: if set, max over cells of |dm/dt| at m_in is atomically maxed in
   const float* hmap;   // per-cell applied field (T) or null
   const float* kumap;  // per-cell Ku (J/m^3) or null
+  const float* drive;  // if set: bx, by, bz, g1, g2 of this evaluation (device), replacing Phys's
+  Tick tick;           // launch_stage: passed to its y/z launch
   int mode;
   int stage;           // RK4 stage 0..3
   unsigned mask;       // mode 0: MM_TERM_* terms to write
@@ -74,6 +101,8 @@ struct mm_ctx {
   double* red_out;           // final reduction result (device)
   int red_blocks;
   int* dflag;                // device error flags: [0] non-finite state, [1] kernel wait timed out
+  ProgState* prog;           // clock, field program and the drive values the stages read
+  int prog_n;                // segments installed
   int cur;                   // Euler: 0 -> state in m0, 1 -> state in stA
   int s_valid;               // S holds the x transform of the current state
   cudaGraphExec_t graph[2];  // RK4: graph[0]; Euler: graph[0] (m0->stA), graph[1] (stA->m0)
@@ -96,6 +125,10 @@ void mm_adjoint_free(mm_ctx* c);
 
 // api.cu
 Phys mm_make_phys(const mm_ctx* c);
+
+// program.cu: stream-ordered writes of the program state (1 launch each)
+int mm_prog_init(mm_ctx* c);        // clock 0, no segments, base and every drive slot from mm_make_phys
+int mm_prog_push_base(mm_ctx* c);   // base <- mm_make_phys (b_ext, alpha); drive slots refreshed at the clock
 
 // One film of a batch, as the batched kernels see it (device array).
 struct BatchFilm {
@@ -150,7 +183,8 @@ int launch_field_part(const Dims& d, const Phys& ph, const StageArgs& a, const f
 int launch_normalise(const Dims& d, float* m, int* flag, cudaStream_t s);
 
 // reduce.cu
-int launch_reduce(const Dims& d, const Phys& ph, const float* m, const float* Hd,
+// drive: if set, bx, by, bz, g1, g2 (device) replacing Phys's
+int launch_reduce(const Dims& d, const Phys& ph, const float* drive, const float* m, const float* Hd,
                   const float* hmap, const float* kumap, double A, double Ku, double delta,
                   double Ms, double* partials, int nblocks, double* out, int* flag,
                   cudaStream_t s);

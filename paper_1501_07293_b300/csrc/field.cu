@@ -24,6 +24,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "bulk.cuh"
+#include "program.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -211,7 +212,8 @@ struct YzLayout {
 
 template <int PY, int NZM>
 __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __restrict__ Kh,
-                                        const float2* __restrict__ twY, const Dims& d, int* flag, int kx) {
+                                        const float2* __restrict__ twY, const Dims& d, int* flag, int kx,
+                                        const Tick& tk = Tick{}) {
   constexpr int T = TeamOf<PY>::v;
   constexpr int PADS = YzLayout<PY>::PADS;
   constexpr int RS = YzLayout<PY>::RS;
@@ -237,6 +239,10 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
     for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) buf[(i / ny) * RS + i % ny] = Sk[i];
   }
   for (int i = threadIdx.x; i < PY; i += blockDim.x) tws[i] = twY[i];
+  // first y/z pass of a step: the last warp of CTA 0 advances the field
+  // program's clock and writes the drive slots while the copies land (the x
+  // kernels that follow read them; nothing in this kernel does)
+  if (tk.p && kx == 0 && threadIdx.x >= blockDim.x - 32) prog_tick(tk);
   if (bulk && !mbar_wait_bounded(&bar, 0)) {
     if (threadIdx.x == 0) atomicOr(flag + 1, 1);
     mbar_wait_bounded(&bar, 0);   // give copies in flight one more bounded chance before leaving
@@ -276,8 +282,8 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
 
 template <int PY, int NZM>
 __global__ void __launch_bounds__(512, 1) k_yz(float2* __restrict__ S, const float* __restrict__ Kh,
-                                                const float2* __restrict__ twY, Dims d, int* flag) {
-  body_yz<PY, NZM>(S, Kh, twY, d, flag, blockIdx.x);
+                                                const float2* __restrict__ twY, Dims d, int* flag, Tick tk) {
+  body_yz<PY, NZM>(S, Kh, twY, d, flag, blockIdx.x, tk);
 }
 
 // ---------------------------------------------------------------------------
@@ -542,9 +548,17 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
   }
 }
 
-template <int HALF>
+// DRIVE: the applied field and LLG prefactors of this stage come from the field
+// program's drive slot (a.drive, device memory) instead of the kernel parameters
+// (a separate instantiation, so the constant-field kernel keeps them as
+// constant-bank operands).
+template <int HALF, bool DRIVE>
 __global__ void __launch_bounds__(512) k_x(StageArgs a, Phys ph, float2* __restrict__ S,
                                            const float2* __restrict__ twP, Dims d, int TY, int fwd) {
+  if constexpr (DRIVE) {
+    ph.bx = a.drive[0]; ph.by = a.drive[1]; ph.bz = a.drive[2];
+    ph.g1 = a.drive[3]; ph.g2 = a.drive[4];
+  }
   body_x<HALF>(a, ph, S, twP, d, TY, fwd, blockIdx.y, blockIdx.x * TY);
 }
 
@@ -647,10 +661,15 @@ static cudaError_t run_x(const Dims& d, const Phys& ph, const StageArgs& a, cons
   threads = (threads + 31) / 32 * 32;
   if (threads < 128) threads = 128;
   if (threads > 512) threads = 512;
-  static bool attr = false;
-  if (cudaError_t e = allow_max_smem(k_x<HALF>, attr)) return e;
+  static bool attr = false, attr_d = false;
   dim3 grid((d.ny + TY - 1) / TY, d.nz, 1);
-  k_x<HALF><<<grid, threads, x_smem(HALF), s>>>(a, ph, S, tw + P, d, TY, fwd);
+  if (a.drive) {
+    if (cudaError_t e = allow_max_smem(k_x<HALF, true>, attr_d)) return e;
+    k_x<HALF, true><<<grid, threads, x_smem(HALF), s>>>(a, ph, S, tw + P, d, TY, fwd);
+  } else {
+    if (cudaError_t e = allow_max_smem(k_x<HALF, false>, attr)) return e;
+    k_x<HALF, false><<<grid, threads, x_smem(HALF), s>>>(a, ph, S, tw + P, d, TY, fwd);
+  }
   return cudaGetLastError();
 }
 
@@ -685,10 +704,11 @@ static cudaError_t dispatch_x(const Dims& d, const Phys& ph, const StageArgs& a,
 
 // --- y/z pass ------------------------------------------------------------------
 template <int PY, int NZM>
-static cudaError_t run_yz_t(const Dims& d, const float2* tw, float2* S, const float* Kh, int* flag, cudaStream_t s) {
+static cudaError_t run_yz_t(const Dims& d, const float2* tw, float2* S, const float* Kh, int* flag, const Tick& tk,
+                            cudaStream_t s) {
   static bool attr = false;
   if (cudaError_t e = allow_max_smem(k_yz<PY, NZM>, attr)) return e;
-  k_yz<PY, NZM><<<d.hx, 512, yz_smem(d), s>>>(S, Kh, tw + PY, d, flag);
+  k_yz<PY, NZM><<<d.hx, 512, yz_smem(d), s>>>(S, Kh, tw + PY, d, flag, tk);
   return cudaGetLastError();
 }
 
@@ -703,25 +723,27 @@ static cudaError_t run_yz_t(const Dims& d, const float2* tw, float2* S, const fl
   return cudaErrorInvalidValue;
 
 template <int PY>
-static cudaError_t run_yz_nz(const Dims& d, const float2* tw, float2* S, const float* Kh, int* flag, cudaStream_t s) {
-#define MM_CALL_YZ(Z) run_yz_t<PY, Z>(d, tw, S, Kh, flag, s)
+static cudaError_t run_yz_nz(const Dims& d, const float2* tw, float2* S, const float* Kh, int* flag, const Tick& tk,
+                             cudaStream_t s) {
+#define MM_CALL_YZ(Z) run_yz_t<PY, Z>(d, tw, S, Kh, flag, tk, s)
   MM_NZ_SWITCH(d.nz, MM_CALL_YZ)
 #undef MM_CALL_YZ
 }
 
-static cudaError_t dispatch_yz(const Dims& d, const float2* tw, float2* S, const float* Kh, int* flag, cudaStream_t s) {
+static cudaError_t dispatch_yz(const Dims& d, const float2* tw, float2* S, const float* Kh, int* flag, const Tick& tk,
+                               cudaStream_t s) {
   switch (d.py) {
-    case 1: return run_yz_nz<1>(d, tw, S, Kh, flag, s);
-    case 4: return run_yz_nz<4>(d, tw, S, Kh, flag, s);
-    case 8: return run_yz_nz<8>(d, tw, S, Kh, flag, s);
-    case 16: return run_yz_nz<16>(d, tw, S, Kh, flag, s);
-    case 32: return run_yz_nz<32>(d, tw, S, Kh, flag, s);
-    case 64: return run_yz_nz<64>(d, tw, S, Kh, flag, s);
-    case 128: return run_yz_nz<128>(d, tw, S, Kh, flag, s);
-    case 256: return run_yz_nz<256>(d, tw, S, Kh, flag, s);
-    case 512: return run_yz_nz<512>(d, tw, S, Kh, flag, s);
-    case 1024: return run_yz_nz<1024>(d, tw, S, Kh, flag, s);
-    case 2048: return run_yz_nz<2048>(d, tw, S, Kh, flag, s);
+    case 1: return run_yz_nz<1>(d, tw, S, Kh, flag, tk, s);
+    case 4: return run_yz_nz<4>(d, tw, S, Kh, flag, tk, s);
+    case 8: return run_yz_nz<8>(d, tw, S, Kh, flag, tk, s);
+    case 16: return run_yz_nz<16>(d, tw, S, Kh, flag, tk, s);
+    case 32: return run_yz_nz<32>(d, tw, S, Kh, flag, tk, s);
+    case 64: return run_yz_nz<64>(d, tw, S, Kh, flag, tk, s);
+    case 128: return run_yz_nz<128>(d, tw, S, Kh, flag, tk, s);
+    case 256: return run_yz_nz<256>(d, tw, S, Kh, flag, tk, s);
+    case 512: return run_yz_nz<512>(d, tw, S, Kh, flag, tk, s);
+    case 1024: return run_yz_nz<1024>(d, tw, S, Kh, flag, tk, s);
+    case 2048: return run_yz_nz<2048>(d, tw, S, Kh, flag, tk, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -730,7 +752,7 @@ static cudaError_t dispatch_yz(const Dims& d, const float2* tw, float2* S, const
 int launch_field_eval(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
                       const float* Kh, int* flag, cudaStream_t s) {
   if (dispatch_xfwd(d, a.m_in, tw, S, s) != cudaSuccess) return -1;
-  if (dispatch_yz(d, tw, S, Kh, flag, s) != cudaSuccess) return -2;
+  if (dispatch_yz(d, tw, S, Kh, flag, Tick{}, s) != cudaSuccess) return -2;
   if (dispatch_x(d, ph, a, tw, S, s, a.mode != 0) != cudaSuccess) return -3;
   return 3;
 }
@@ -739,7 +761,7 @@ int launch_field_eval(const Dims& d, const Phys& ph, const StageArgs& a, const f
 // + update + x forward of the new state (S then holds the transform of a.m_out).
 int launch_stage(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
                  const float* Kh, int* flag, cudaStream_t s) {
-  if (dispatch_yz(d, tw, S, Kh, flag, s) != cudaSuccess) return -2;
+  if (dispatch_yz(d, tw, S, Kh, flag, a.tick, s) != cudaSuccess) return -2;
   if (dispatch_x(d, ph, a, tw, S, s, 1) != cudaSuccess) return -3;
   return 2;
 }
@@ -752,7 +774,7 @@ int launch_field_part(const Dims& d, const Phys& ph, const StageArgs& a, const f
                       const float* Kh, int* flag, cudaStream_t s, int part) {
   cudaError_t e = cudaErrorInvalidValue;
   if (part == 0) e = dispatch_xfwd(d, a.m_in, tw, S, s);
-  else if (part == 1) e = dispatch_yz(d, tw, S, Kh, flag, s);
+  else if (part == 1) e = dispatch_yz(d, tw, S, Kh, flag, a.tick, s);
   else if (part == 2) e = dispatch_x(d, ph, a, tw, S, s, a.mode != 0);
   return e == cudaSuccess ? 1 : -1;
 }

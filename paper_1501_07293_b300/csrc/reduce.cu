@@ -32,7 +32,9 @@ struct RedParams {
 
 __global__ void __launch_bounds__(256) k_reduce(const float* __restrict__ m, const float* __restrict__ Hd,
                                                 const float* __restrict__ hmap, const float* __restrict__ kumap,
-                                                Dims d, Phys ph, RedParams rp, double* __restrict__ partials) {
+                                                Dims d, Phys ph, const float* __restrict__ drive, RedParams rp,
+                                                double* __restrict__ partials) {
+  if (drive) { ph.bx = drive[0]; ph.by = drive[1]; ph.bz = drive[2]; ph.g1 = drive[3]; ph.g2 = drive[4]; }
   double acc[NRED];
 #pragma unroll
   for (int j = 0; j < NRED; ++j) acc[j] = 0.0;
@@ -113,7 +115,7 @@ __global__ void k_reduce_final(const double* __restrict__ partials, int nblocks,
   if (j == 8 && v > 0.0) atomicOr(flag, 1);
 }
 
-int launch_reduce(const Dims& d, const Phys& ph, const float* m, const float* Hd, const float* hmap,
+int launch_reduce(const Dims& d, const Phys& ph, const float* drive, const float* m, const float* Hd, const float* hmap,
                   const float* kumap, double A, double Ku, double delta, double Ms, double* partials,
                   int nblocks, double* out, int* flag, cudaStream_t s) {
   RedParams rp;
@@ -122,7 +124,7 @@ int launch_reduce(const Dims& d, const Phys& ph, const float* m, const float* Hd
   rp.Ku_d3 = Ku * rp.d3;
   rp.demag_pref = -0.5 * MM_MU0 * rp.d3 * Ms;
   rp.zee_pref = -rp.d3 * Ms;
-  k_reduce<<<nblocks, 256, 0, s>>>(m, Hd, hmap, kumap, d, ph, rp, partials);
+  k_reduce<<<nblocks, 256, 0, s>>>(m, Hd, hmap, kumap, d, ph, drive, rp, partials);
   if (cudaGetLastError() != cudaSuccess) return -1;
   k_reduce_final<<<1, 32, 0, s>>>(partials, nblocks, 1.0 / (double)d.N, out, flag);
   if (cudaGetLastError() != cudaSuccess) return -1;

@@ -202,3 +202,57 @@ def film_batch(nfilms: int = 256, nx_range=(32, 256), ny_range=(8, 128),
 BATCH_MATERIAL = Material(Ms=8.0e5, A=1.3e-11, Ku=0.0, alpha=0.5, gamma=1.76e11)
 BATCH_DELTA = 5e-9
 BATCH_DT = 1e-13
+
+
+# ---------------------------------------------------------------------------
+# the standard-problem-4 protocol (Section 3, script of Appendix A)
+# ---------------------------------------------------------------------------
+
+_MU0 = 4.0e-7 * np.pi     # only to convert the schedule's kA/m values to tesla
+_KAM = 1e3 * _MU0         # 1 kA/m of H as mu0 H, tesla
+
+
+def sp4_film() -> Workload:
+    """The paper's validation film: 500x125x3 nm as 166x42x1 cells of 3 nm,
+    Ms 800 kA/m, A 1.3e-11 J/m, no anisotropy, damping 0.5 while relaxing,
+    explicit Euler with dt = 5 fs for 150,000 steps, starting along x.
+    gamma = 2.21e5 / mu0 is the gyromagnetic ratio the script's LLG prefactor
+    (0.221 in its nm/ns/kA/m units) stands for."""
+    return Workload("sp4_166x42x1", (166, 42, 1), 3e-9,
+                    Material(Ms=8.0e5, A=1.3e-11, Ku=0.0, alpha=0.5, gamma=2.21e5 / _MU0),
+                    (0.0, 0.0, 0.0), 5e-15, 150000, "uniform_x", 0)
+
+
+def sp4_schedule(dt: float, n_sat: int = 4000, n_ramp: int = 6000, n_rev: int = 50000,
+                 n_end: int = 150000, h_sat_kam: float = 100.0,
+                 h_rev_kam=(-19.576, 3.422, 0.0), alpha_relax: float = 0.5,
+                 alpha_rev: float = 0.02) -> list:
+    """Field program segments (t_begin, t_end, b_begin, b_end, alpha) of the
+    standard-problem-4 protocol, times in s and fields in tesla.
+
+    The script counts steps t = 1, 2, ... and its step t moves the state from
+    time (t - 1) dt to t dt with the field of index t; the segments below put
+    that field at the step's start time n dt, n = t - 1:
+      t < n_sat               h_sat along each of x, y, z            (saturate)
+      n_sat <= t < n_ramp     h_sat (n_ramp - t) / (n_ramp - n_sat)   on each
+                              component (the script's /20 for the default
+                              2000-step ramp)                          (ramp down)
+      n_ramp <= t <= n_rev    zero field
+      t > n_rev               h_rev, damping alpha_rev                (reverse)
+    Reading: the script's ramp lines add the ramp three times to H_x and none
+    to H_y, H_z; the text says the saturating field along (1, 1, 1) is slowly
+    reduced, so the ramp applies to each component (continuous with the
+    saturation phase).  The discontinuous switch to the reverse field sits half
+    a step before step index n_rev + 1 so that no rounding of the clock can move
+    it by a step; the continuous ramp ends stay on step times.
+    """
+    sat = (h_sat_kam * _KAM,) * 3
+    zero = (0.0, 0.0, 0.0)
+    rev = tuple(h * _KAM for h in h_rev_kam)
+    t_sat, t_ramp, t_rev = (n_sat - 1) * dt, (n_ramp - 1) * dt, (n_rev - 0.5) * dt
+    return [
+        (0.0, t_sat, sat, sat, alpha_relax),
+        (t_sat, t_ramp, sat, zero, alpha_relax),
+        (t_ramp, t_rev, zero, zero, alpha_relax),
+        (t_rev, (n_end + 1) * dt, rev, rev, alpha_rev),
+    ]

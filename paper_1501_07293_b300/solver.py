@@ -34,6 +34,13 @@ class Opts(ctypes.Structure):
                 ("obs_every", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
+class Segment(ctypes.Structure):
+    """mm_segment: [t_begin, t_end) s, b_begin/b_end (T, linear in between), alpha (< 0: context's)."""
+    _fields_ = [("t_begin", ctypes.c_double), ("t_end", ctypes.c_double), ("b_begin", ctypes.c_double * 3),
+                ("b_end", ctypes.c_double * 3), ("alpha", ctypes.c_double)]
+
+
+PROGRAM_MAX = 32
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -47,6 +54,9 @@ _SIGNATURES = {
     "mm_get_m": (_I, [_P, _P]),
     "mm_set_field": (_I, [_P, ctypes.POINTER(_D), _P, _P]),
     "mm_set_alpha": (_I, [_P, _D]),
+    "mm_set_program": (_I, [_P, _I, ctypes.POINTER(Segment)]),
+    "mm_set_time": (_I, [_P, _D]),
+    "mm_get_time": (_I, [_P, ctypes.POINTER(_D)]),
     "mm_heff": (_I, [_P, _P, ctypes.c_uint]),
     "mm_step": (_I, [_P, _I, _D]),
     "mm_energy": (_I, [_P, ctypes.POINTER(_D)]),
@@ -180,6 +190,25 @@ class Solver:
 
     def set_alpha(self, alpha: float):
         self._check(self._L.mm_set_alpha(self.ctx, float(alpha)))
+
+    def set_program(self, segments):
+        """Field program: iterable of (t_begin, t_end, b_begin[3], b_end[3], alpha); [] removes it."""
+        segs = list(segments)
+        arr = (Segment * max(1, len(segs)))()
+        for i, (t0, t1, b0, b1, al) in enumerate(segs):
+            arr[i].t_begin, arr[i].t_end, arr[i].alpha = float(t0), float(t1), float(al)
+            for k in range(3):
+                arr[i].b_begin[k], arr[i].b_end[k] = float(b0[k]), float(b1[k])
+        self._check(self._L.mm_set_program(self.ctx, len(segs), arr))
+
+    def set_time(self, t: float):
+        self._check(self._L.mm_set_time(self.ctx, float(t)))
+
+    def time(self) -> float:
+        """The context clock (s); synchronises."""
+        v = _D(0.0)
+        self._check(self._L.mm_get_time(self.ctx, ctypes.byref(v)))
+        return v.value
 
     def heff(self, mask: int = TERM_ALL, out=None):
         t = self.torch
