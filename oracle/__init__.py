@@ -28,6 +28,11 @@ Which pin checks which function (tests/test_oracle_*.py, ``-m "not gpu"``):
                Euler order 1, |m| = 1 after renormalisation
   energy.py    pair-sum identity of the exchange energy, energy decay with
                damping, dE/dt = -mu0 Ms delta^3 sum H . dm/dt
+  program.py   the appendix script's schedule conditions per step index,
+               macrospin closed form under ramps and a damping switch,
+               constant program == constant field, Euler across a switch
+               == concatenated constant runs
+  adjoint.py   central finite differences of the oracle's own trajectory
 Parity unpinned: nothing in this oracle is checked against a printed
 trajectory (the paper's Fig. 3 comparison with OOMMF has no data in the text).
 """
