@@ -312,6 +312,38 @@ def bench_sp4(args, sample_every=1000):
     return out
 
 
+TABLE1_GPU_SINGLE_MS = {8: 22.58, 16: 23.97, 32: 26.89, 64: 76.24}   # the paper's Table 1 (GTX 650 Ti)
+
+
+def bench_sp3(args, steps=500, warmup=20):
+    """Table 1's shapes: per-step time of explicit Euler on the standard-problem-3
+    cube, n = 8 .. 64, graph replays, working set resident in L2 (as in the
+    paper's steady-state loop).  The paper's GTX 650 Ti numbers are context."""
+    import torch
+    from paper_1501_07293_b300 import inputs
+    from paper_1501_07293_b300.solver import Solver
+    stream = torch.cuda.current_stream()
+    rows = []
+    for n in (8, 16, 32, 64):
+        w = inputs.sp3_cube(n)
+        mat = w.mat
+        s = Solver(w.grid, w.delta, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma, integrator="euler")
+        s.set_m(torch.from_numpy(inputs.workload_state(w)).cuda())
+        s.step(warmup, w.dt)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(steps, w.dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        rows.append({"n": n, "ms_per_step": ms, "cell_steps_per_s": n ** 3 / (ms * 1e-3),
+                     "paper_gtx650ti_single_ms": TABLE1_GPU_SINGLE_MS[n]})
+        s.close()
+    return {"workload": "muMAG standard problem 3 cube n^3, Euler, FP32, one field evaluation per step",
+            "steps": steps, "rows": rows}
+
+
 def b300_arm(args, w):
     import torch
     import torch.distributed as dist
@@ -412,6 +444,7 @@ def b300_arm(args, w):
         extra["batched"] = bench_batched(args)
         extra["adjoint"] = bench_adjoint(args)
         extra["sp4_protocol"] = bench_sp4(args)
+        extra["sp3_table1"] = bench_sp3(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -147,8 +147,7 @@ __device__ __forceinline__ void zprod(int a, const float2* __restrict__ buf, int
 #pragma unroll
       for (int zi = 0; zi < NZM; ++zi) {
         const float k = (zo >= zi) ? kr[zo - zi] : kn[zi - zo];
-        out[zo].x = fmaf(k, mv[zi].x, out[zo].x);
-        out[zo].y = fmaf(k, mv[zi].y, out[zo].y);
+        out[zo] = __ffma2_rn(make_float2(k, k), mv[zi], out[zo]);   // packed FP32 pair
       }
     }
   }
@@ -179,6 +178,86 @@ __device__ __forceinline__ void zprod_column(float2* buf, int rs, int len, int n
 #pragma unroll
       for (int zo = 0; zo < NZM; ++zo)
         if (zo < nz) buf[(a * nz + zo) * rs + pidx<PADS>(k)] = out[zo];
+    }
+    __syncwarp();
+  }
+}
+
+// Thick films (NZM = 32, 64): the same product with each lane owning one chunk
+// of 16 output planes.  The input planes are walked in blocks of 16; between
+// input block j and output chunk c the offsets zo - zi span 16 (c - j) - 15 ..
+// 16 (c - j) + 15, a window of 31 kernel values loaded once per block.
+// Offsets with |zo - zi| >= nz only meet zero inputs or discarded outputs and
+// are read as zeros.
+__device__ __forceinline__ void zprod_chunk(int a, int c, const float2* __restrict__ buf, int rs, int pos, int nz,
+                                            const float* __restrict__ Kk, int kyf, bool mirrored,
+                                            float2 (&out)[16]) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) out[q] = make_float2(0.f, 0.f);
+  const int nblk = (nz + 15) >> 4;
+#pragma unroll 1
+  for (int b = 0; b < 3; ++b) {
+    const int p = (a == b) ? a : 2 + a + b;
+    const bool odd_y = (p == 3 || p == 5);
+    const bool odd_z = (p >= 4);
+    const float ys = (mirrored && odd_y) ? -1.f : 1.f;
+    const float zs = odd_z ? -ys : ys;
+    const float* kp = Kk + ((long long)kyf * 6 + p) * nz;
+#pragma unroll 1
+    for (int j = 0; j < nblk; ++j) {
+      const int base = 16 * (c - j) - 15;
+      float w[31];
+#pragma unroll
+      for (int t = 0; t < 31; ++t) {
+        const int off = base + t;
+        const int q = off < 0 ? -off : off;
+        const float v = q < nz ? __ldg(kp + q) : 0.f;
+        w[t] = (off < 0 ? zs : ys) * v;
+      }
+      float2 mv[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int zi = 16 * j + i;
+        const float2 v = zi < nz ? buf[(b * nz + zi) * rs + pos] : make_float2(0.f, 0.f);
+        mv[i] = odd_z ? make_float2(-v.y, v.x) : v;
+      }
+#pragma unroll
+      for (int zo = 0; zo < 16; ++zo) {
+#pragma unroll
+        for (int zi = 0; zi < 16; ++zi) {
+          const float k = w[zo - zi + 15];
+          out[zo] = __ffma2_rn(make_float2(k, k), mv[zi], out[zo]);
+        }
+      }
+    }
+  }
+}
+
+// Lanes take (position, output component, chunk): 3 NZM/16 lanes per position,
+// all in one warp, so the in-place write-back again needs only __syncwarp.
+template <int NZM, int PADS, typename KyOf>
+__device__ __forceinline__ void zprod_column_chunked(float2* buf, int rs, int len, int nz,
+                                                     const float* __restrict__ Kk, int py, KyOf ky_of) {
+  constexpr int NCH = NZM / 16;
+  constexpr int LPK = 3 * NCH;      // lanes per position
+  constexpr int KPW = 32 / LPK;     // positions per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int kl = lane / LPK, r = lane % LPK, a = r / NCH, c = r % NCH;
+  const int ntasks = (len + KPW - 1) / KPW;
+  for (int task = warp; task < ntasks; task += nwarps) {
+    const int k = task * KPW + kl;
+    const bool act = kl < KPW && k < len && 16 * c < nz;
+    float2 out[16];
+    if (act) {
+      const int ky = ky_of(k);
+      const bool mirrored = ky > py / 2;
+      zprod_chunk(a, c, buf, rs, pidx<PADS>(k), nz, Kk, mirrored ? py - ky : ky, mirrored, out);
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int zo = 0; zo < 16; ++zo)
+        if (16 * c + zo < nz) buf[(a * nz + 16 * c + zo) * rs + pidx<PADS>(k)] = out[zo];
     }
     __syncwarp();
   }
@@ -258,7 +337,10 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
     __syncthreads();
   }
   // Product of eq. 14 along z (see zprod).
-  if (PY > 1)
+  if constexpr (NZM > 16)
+    zprod_column_chunked<NZM, (PY > 1 ? PADS : 0)>(buf, RS, PY, nz, Kh + (long long)kx * d.hy * 6 * nz, PY,
+                                                   KyIdentity());
+  else if (PY > 1)
     zprod_column<NZM, PADS>(buf, RS, PY, nz, Kh + (long long)kx * d.hy * 6 * nz, d.hy, PY, KyIdentity());
   else
     zprod_column<NZM, 0>(buf, RS, PY, nz, Kh + (long long)kx * 6 * nz * d.hy, d.hy, PY, KyIdentity());
@@ -621,8 +703,8 @@ int mm_supported(const Dims& d, char* why, int nwhy) {
     snprintf(why, nwhy, "padded size %dx%d exceeds 2048 (nx, ny <= 1024 supported)", d.px, d.py);
     return 0;
   }
-  if (d.nz > 16) {
-    snprintf(why, nwhy, "nz = %d > 16 is not supported by the z Toeplitz product of this build", d.nz);
+  if (d.nz > 64) {
+    snprintf(why, nwhy, "nz = %d > 64 is not supported by the z Toeplitz product of this build", d.nz);
     return 0;
   }
   const size_t need = yz_smem(d);
@@ -725,6 +807,16 @@ static cudaError_t run_yz_t(const Dims& d, const float2* tw, float2* S, const fl
 template <int PY>
 static cudaError_t run_yz_nz(const Dims& d, const float2* tw, float2* S, const float* Kh, int* flag, const Tick& tk,
                              cudaStream_t s) {
+  // thick films: a column of 3 x 64 planes fits shared memory up to PY = 128,
+  // of 3 x 32 planes up to PY = 256
+  if (nzm_of(d.nz) == 64) {
+    if constexpr (PY <= 128) return run_yz_t<PY, 64>(d, tw, S, Kh, flag, tk, s);
+    return cudaErrorInvalidValue;
+  }
+  if (nzm_of(d.nz) == 32) {
+    if constexpr (PY <= 256) return run_yz_t<PY, 32>(d, tw, S, Kh, flag, tk, s);
+    return cudaErrorInvalidValue;
+  }
 #define MM_CALL_YZ(Z) run_yz_t<PY, Z>(d, tw, S, Kh, flag, tk, s)
   MM_NZ_SWITCH(d.nz, MM_CALL_YZ)
 #undef MM_CALL_YZ

@@ -256,3 +256,27 @@ def sp4_schedule(dt: float, n_sat: int = 4000, n_ramp: int = 6000, n_rev: int = 
         (t_ramp, t_rev, zero, zero, alpha_relax),
         (t_rev, (n_end + 1) * dt, rev, rev, alpha_rev),
     ]
+
+
+# ---------------------------------------------------------------------------
+# the standard-problem-3 cube (Section 3, Table 1)
+# ---------------------------------------------------------------------------
+
+SP3_EDGE_LEX = 8.5   # cube edge in exchange lengths, near the flower/vortex crossover of the problem
+
+
+def sp3_cube(n: int) -> Workload:
+    """The paper's timing problem: an n x n x n cube, A 1e-11 J/m, Ms 1000 kA/m,
+    anisotropy field 100 kA/m (Ku = mu0 Ms H_K / 2, easy axis x as in the
+    paper's anisotropy code), large damping (1.0), explicit Euler.  The paper
+    does not give the cube's size; it is taken as 8.5 exchange lengths
+    (l_ex = sqrt(2A / (mu0 Ms^2)) = 3.99 nm), cut into n^3 cells.  dt keeps
+    gamma * (largest exchange field) * dt at 0.05 so that every n is stable."""
+    Ms, A, HK = 1.0e6, 1.0e-11, 1.0e5
+    lex = np.sqrt(2.0 * A / (_MU0 * Ms * Ms))
+    delta = SP3_EDGE_LEX * lex / n
+    b_ex = 12.0 * A / (Ms * delta * delta)   # tesla: 6 neighbours of 2A/(Ms delta^2) at opposite sign
+    dt = 0.05 / (1.76e11 * b_ex)
+    return Workload(f"sp3_cube_{n}", (n, n, n), delta,
+                    Material(Ms=Ms, A=A, Ku=0.5 * _MU0 * Ms * HK, alpha=1.0, gamma=1.76e11),
+                    (0.0, 0.0, 0.0), dt, 1000, "vortex", 3000 + n)
