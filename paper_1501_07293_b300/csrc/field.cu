@@ -318,6 +318,13 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
     for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) buf[(i / ny) * RS + i % ny] = Sk[i];
   }
   for (int i = threadIdx.x; i < PY; i += blockDim.x) tws[i] = twY[i];
+  {
+    // the column's slice of the transformed tensor is first read by the z
+    // product, after the transforms: start bringing it into L2 now
+    const char* kc = reinterpret_cast<const char*>(Kh + (long long)kx * d.hy * 6 * nz);
+    const int nlines = (d.hy * 6 * nz * (int)sizeof(float) + 127) >> 7;
+    for (int i = threadIdx.x; i < nlines; i += blockDim.x) prefetch_l2(kc + ((long long)i << 7));
+  }
   // first y/z pass of a step: the last warp of CTA 0 advances the field
   // program's clock and writes the drive slots while the copies land (the x
   // kernels that follow read them; nothing in this kernel does)
@@ -375,6 +382,47 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
   return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
+// Eq. 2 on the unit vector m in the total field B (tesla), then the integrator:
+// mode 2 the explicit Euler step, mode 1 RK4 stage a.stage with base state m0
+// and accumulator value accv (read for stages 1..3).  Returns the next stage
+// state (renormalised after a full step); *acc_out is the accumulator to store
+// (stages 0..2), *kmag |dm/dt| at m.
+__device__ __forceinline__ float3 llg_stage(const StageArgs& a, const Phys& ph, float3 m, float3 B, float3 m0,
+                                            float3 accv, float3* acc_out, float* kmag) {
+  // dm/dt = g1 m x B + g2 m x (m x B)
+  const float3 mxB = cross3(m, B);
+  const float3 mxmxB = cross3(m, mxB);
+  const float3 k = make_float3(ph.g1 * mxB.x + ph.g2 * mxmxB.x, ph.g1 * mxB.y + ph.g2 * mxmxB.y,
+                               ph.g1 * mxB.z + ph.g2 * mxmxB.z);
+  if (kmag) *kmag = sqrtf(k.x * k.x + k.y * k.y + k.z * k.z);
+  float3 nm;
+  bool renorm = false;
+  if (a.mode == 2) {
+    nm = make_float3(m.x + a.dt * k.x, m.y + a.dt * k.y, m.z + a.dt * k.z);
+    renorm = true;
+  } else if (a.stage == 0) {
+    *acc_out = k;
+    const float h = 0.5f * a.dt;
+    nm = make_float3(m0.x + h * k.x, m0.y + h * k.y, m0.z + h * k.z);
+  } else if (a.stage < 3) {
+    float3 s = accv;
+    s.x = fmaf(2.f, k.x, s.x); s.y = fmaf(2.f, k.y, s.y); s.z = fmaf(2.f, k.z, s.z);
+    *acc_out = s;
+    const float h = (a.stage == 1) ? 0.5f * a.dt : a.dt;
+    nm = make_float3(m0.x + h * k.x, m0.y + h * k.y, m0.z + h * k.z);
+  } else {
+    const float3 s = make_float3(accv.x + k.x, accv.y + k.y, accv.z + k.z);
+    const float h = a.dt * (1.0f / 6.0f);
+    nm = make_float3(m0.x + h * s.x, m0.y + h * s.y, m0.z + h * s.z);
+    renorm = true;
+  }
+  if (renorm) {
+    const float inv = rsqrtf(nm.x * nm.x + nm.y * nm.y + nm.z * nm.z);
+    nm.x *= inv; nm.y *= inv; nm.z *= inv;
+  }
+  return nm;
+}
+
 // One cell given its demag field bd (tesla).  Mode 0 writes H; modes 1/2 write
 // and return the next stage / new state.
 __device__ __forceinline__ float3 cell_update(const StageArgs& a, const Phys& ph, const Dims& d,
@@ -427,46 +475,124 @@ __device__ __forceinline__ float3 cell_update(const StageArgs& a, const Phys& ph
     a.B_out[cell + N] = B.y;
     a.B_out[cell + 2 * N] = B.z;
   }
-  // eq. 2 on the unit vector: dm/dt = g1 m x B + g2 m x (m x B)
-  const float3 mxB = cross3(m, B);
-  const float3 mxmxB = cross3(m, mxB);
-  const float3 k = make_float3(ph.g1 * mxB.x + ph.g2 * mxmxB.x, ph.g1 * mxB.y + ph.g2 * mxmxB.y,
-                               ph.g1 * mxB.z + ph.g2 * mxmxB.z);
-  if (kmag) *kmag = sqrtf(k.x * k.x + k.y * k.y + k.z * k.z);   // |dm/dt| at m_in
-  float3 nm;
-  bool renorm = false;
-  if (a.mode == 2) {
-    nm = make_float3(m.x + a.dt * k.x, m.y + a.dt * k.y, m.z + a.dt * k.z);
-    renorm = true;
-  } else {
-    float* acc = a.acc;
-    const float* m0p = a.m0;
-    const float3 m0 = make_float3(m0p[cell], m0p[cell + N], m0p[cell + 2 * N]);
-    if (a.stage == 0) {
-      acc[cell] = k.x; acc[cell + N] = k.y; acc[cell + 2 * N] = k.z;
-      const float h = 0.5f * a.dt;
-      nm = make_float3(m0.x + h * k.x, m0.y + h * k.y, m0.z + h * k.z);
-    } else if (a.stage < 3) {
-      float3 s = make_float3(acc[cell], acc[cell + N], acc[cell + 2 * N]);
-      s.x = fmaf(2.f, k.x, s.x); s.y = fmaf(2.f, k.y, s.y); s.z = fmaf(2.f, k.z, s.z);
-      acc[cell] = s.x; acc[cell + N] = s.y; acc[cell + 2 * N] = s.z;
-      const float h = (a.stage == 1) ? 0.5f * a.dt : a.dt;
-      nm = make_float3(m0.x + h * k.x, m0.y + h * k.y, m0.z + h * k.z);
-    } else {
-      const float3 s = make_float3(acc[cell] + k.x, acc[cell + N] + k.y, acc[cell + 2 * N] + k.z);
-      const float h = a.dt * (1.0f / 6.0f);
-      nm = make_float3(m0.x + h * s.x, m0.y + h * s.y, m0.z + h * s.z);
-      renorm = true;
-    }
+  float3 m0 = m, accv = m;
+  if (a.mode == 1) {
+    m0 = make_float3(a.m0[cell], a.m0[cell + N], a.m0[cell + 2 * N]);
+    if (a.stage > 0) accv = make_float3(a.acc[cell], a.acc[cell + N], a.acc[cell + 2 * N]);
   }
-  if (renorm) {
-    const float inv = rsqrtf(nm.x * nm.x + nm.y * nm.y + nm.z * nm.z);
-    nm.x *= inv; nm.y *= inv; nm.z *= inv;
+  float3 acc_out;
+  const float3 nm = llg_stage(a, ph, m, B, m0, accv, &acc_out, kmag);
+  if (a.mode == 1 && a.stage < 3) {
+    a.acc[cell] = acc_out.x; a.acc[cell + N] = acc_out.y; a.acc[cell + 2 * N] = acc_out.z;
   }
   a.m_out[cell] = nm.x;
   a.m_out[cell + N] = nm.y;
   a.m_out[cell + 2 * N] = nm.z;
   return nm;
+}
+
+// V (2 or 4) consecutive cells x0 .. x0+V-1 of row (y, z) in modes 1/2 (nx a
+// multiple of V, so every row and plane offset keeps the vector alignment):
+// the same arithmetic as cell_update, with V-wide loads and stores.  The x
+// neighbours inside the group come from the group's own load; the two outside
+// it are scalar loads (clamped at the film edge by eq. 7).
+template <int V> struct VecOf;
+template <> struct VecOf<2> {
+  using T = float2;
+  __device__ static void get(const T& v, float* o) { o[0] = v.x; o[1] = v.y; }
+  __device__ static T make(const float* o) { return make_float2(o[0], o[1]); }
+};
+template <> struct VecOf<4> {
+  using T = float4;
+  __device__ static void get(const T& v, float* o) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+  __device__ static T make(const float* o) { return make_float4(o[0], o[1], o[2], o[3]); }
+};
+
+template <int V>
+__device__ __forceinline__ void cell_updateV(const StageArgs& a, const Phys& ph, const Dims& d, int x0, int y,
+                                             int z, const float3 (&bd)[V], float3 (&nm)[V], float* kmag) {
+  using Vec = VecOf<V>;
+  using T = typename Vec::T;
+  const long long N = d.N;
+  const long long cell = ((long long)z * d.ny + y) * d.nx + x0;
+  const long long row = d.nx, pl = (long long)d.nx * d.ny;
+  const long long oym = y > 0 ? -row : 0, oyp = y < d.ny - 1 ? row : 0;
+  const long long ozm = z > 0 ? -pl : 0, ozp = z < d.nz - 1 ? pl : 0;
+  float mv[3][V], lap[3][V];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float* b = a.m_in + cell + c * N;
+    float sv[V + 2], vym[V], vyp[V], vzm[V], vzp[V];
+    Vec::get(__ldg(reinterpret_cast<const T*>(b)), sv + 1);
+    sv[0] = x0 > 0 ? __ldg(b - 1) : sv[1];
+    sv[V + 1] = x0 + V < d.nx ? __ldg(b + V) : sv[V];
+    Vec::get(__ldg(reinterpret_cast<const T*>(b + oym)), vym);
+    Vec::get(__ldg(reinterpret_cast<const T*>(b + oyp)), vyp);
+    Vec::get(__ldg(reinterpret_cast<const T*>(b + ozm)), vzm);
+    Vec::get(__ldg(reinterpret_cast<const T*>(b + ozp)), vzp);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const float m = sv[j + 1];
+      mv[c][j] = m;
+      lap[c][j] = ((sv[j] - m) + (sv[j + 2] - m)) + ((vym[j] - m) + (vyp[j] - m)) + ((vzm[j] - m) + (vzp[j] - m));
+    }
+  }
+  float can[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) can[j] = ph.c_an;
+  if (a.kumap) {
+    float ku[V];
+    Vec::get(__ldg(reinterpret_cast<const T*>(a.kumap + cell)), ku);
+#pragma unroll
+    for (int j = 0; j < V; ++j) can[j] = ph.c_an_map * ku[j];
+  }
+  float hz[3][V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) { hz[0][j] = ph.bx; hz[1][j] = ph.by; hz[2][j] = ph.bz; }
+  if (a.hmap) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float h[V];
+      Vec::get(__ldg(reinterpret_cast<const T*>(a.hmap + cell + c * N)), h);
+#pragma unroll
+      for (int j = 0; j < V; ++j) hz[c][j] += h[j];
+    }
+  }
+  float m0v[3][V], accv[3][V];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int j = 0; j < V; ++j) { m0v[c][j] = mv[c][j]; accv[c][j] = mv[c][j]; }
+    if (a.mode == 1) {
+      Vec::get(*reinterpret_cast<const T*>(a.m0 + cell + c * N), m0v[c]);
+      if (a.stage > 0) Vec::get(*reinterpret_cast<const T*>(a.acc + cell + c * N), accv[c]);
+    }
+  }
+  float Bv[3][V], ao[3][V], no[3][V];
+  float km = 0.f;
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const float3 m = make_float3(mv[0][j], mv[1][j], mv[2][j]);
+    const float bex_x = ph.c_ex * lap[0][j], bex_y = ph.c_ex * lap[1][j], bex_z = ph.c_ex * lap[2][j];
+    const float ban = can[j] * m.x;
+    const float3 B = make_float3(bex_x + ban + bd[j].x + hz[0][j], bex_y + bd[j].y + hz[1][j],
+                                 bex_z + bd[j].z + hz[2][j]);
+    Bv[0][j] = B.x; Bv[1][j] = B.y; Bv[2][j] = B.z;
+    float3 acc_out = make_float3(0.f, 0.f, 0.f);
+    float kj = 0.f;
+    nm[j] = llg_stage(a, ph, m, B, make_float3(m0v[0][j], m0v[1][j], m0v[2][j]),
+                      make_float3(accv[0][j], accv[1][j], accv[2][j]), &acc_out, kmag ? &kj : nullptr);
+    km = fmaxf(km, kj);
+    ao[0][j] = acc_out.x; ao[1][j] = acc_out.y; ao[2][j] = acc_out.z;
+    no[0][j] = nm[j].x; no[1][j] = nm[j].y; no[2][j] = nm[j].z;
+  }
+  if (kmag) *kmag = km;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (a.B_out) *reinterpret_cast<T*>(a.B_out + cell + c * N) = Vec::make(Bv[c]);
+    if (a.mode == 1 && a.stage < 3) *reinterpret_cast<T*>(a.acc + cell + c * N) = Vec::make(ao[c]);
+    *reinterpret_cast<T*>(a.m_out + cell + c * N) = Vec::make(no[c]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -520,6 +646,7 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
     constexpr int PADS = 4;
     constexpr int RS = HALF + (HALF + 1) / 16 + 2;
     constexpr int TY = XTile<HALF>::v;   // rows per tile (the launcher uses the same value)
+    constexpr int XV = 2;                 // cells per thread of the vector update
     extern __shared__ float2 sm[];
     float2* tws = sm;
     float2* rows = sm + P;   // [3][TY] rows, element k at pidx(k), k <= HALF
@@ -564,6 +691,36 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
     for (int rr = team; rr < NR; rr += nteams) team_fft<HALF, T, 1, 2, PADS>(rows + rr * RS, t, mask, tws);
     __syncthreads();
     float kmax = 0.f;
+    if (a.mode != 0 && (d.nx % XV) == 0) {
+      // XV consecutive cells per thread (vector loads and stores)
+      constexpr int Q = HALF / XV;
+      for (int i = threadIdx.x; i < TY * Q; i += blockDim.x) {
+        const int r = i / Q, x0 = (i % Q) * XV;
+        if (x0 >= d.nx) continue;
+        const int y = y0 + r;
+        if (y >= d.ny) continue;
+        float2* rw[3] = {rows + (0 * TY + r) * RS, rows + (1 * TY + r) * RS, rows + (2 * TY + r) * RS};
+        float3 bd[XV], nm[XV];
+#pragma unroll
+        for (int h = 0; h < XV / 2; ++h) {
+          const float2 p0 = rw[0][pidx<PADS>((x0 >> 1) + h)], p1 = rw[1][pidx<PADS>((x0 >> 1) + h)],
+                       p2 = rw[2][pidx<PADS>((x0 >> 1) + h)];
+          bd[2 * h] = make_float3(ph.c_d * p0.x, ph.c_d * p1.x, ph.c_d * p2.x);
+          bd[2 * h + 1] = make_float3(ph.c_d * p0.y, ph.c_d * p1.y, ph.c_d * p2.y);
+        }
+        float km = 0.f;
+        cell_updateV<XV>(a, ph, d, x0, y, z, bd, nm, a.maxdmdt ? &km : nullptr);
+        kmax = fmaxf(kmax, km);
+        if (fwd) {
+#pragma unroll
+          for (int h = 0; h < XV / 2; ++h) {
+            rw[0][pidx<PADS>((x0 >> 1) + h)] = make_float2(nm[2 * h].x, nm[2 * h + 1].x);
+            rw[1][pidx<PADS>((x0 >> 1) + h)] = make_float2(nm[2 * h].y, nm[2 * h + 1].y);
+            rw[2][pidx<PADS>((x0 >> 1) + h)] = make_float2(nm[2 * h].z, nm[2 * h + 1].z);
+          }
+        }
+      }
+    } else
     for (int i = threadIdx.x; i < TY * HALF; i += blockDim.x) {
       const int r = i / HALF, x = i % HALF;   // nx <= HALF
       if (x >= d.nx) continue;
