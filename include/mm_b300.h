@@ -61,7 +61,15 @@ enum {
 };
 
 typedef struct {
-  int precision;    /* MM_FP32 (only value implemented)                                  */
+  int precision;    /* MM_FP32 (default): the demag product along z as an FP32 direct
+                       sum.  MM_SPLIT_BF16 / MM_SPLIT_FP16: that product through a
+                       length-2nz DFT along z computed as GEMMs on the tensor cores
+                       (tcgen05) with 16-bit hi+lo split operands (x = hi + lo,
+                       products hi*hi + hi*lo + lo*hi, FP32 accumulation; FP16 with
+                       the data scaled by 2^-12); everything else stays FP32.
+                       Split modes need 5 <= nz <= 16 and ny >= 33 (MM_EUNSUPPORTED
+                       otherwise); the effective field then agrees with the FP32
+                       path to ~1e-5 relative.  The paper computes in FP32/FP64 only. */
   int integrator;   /* MM_RK4 (classical, renormalise after the full step) or MM_EULER
                        (the paper's explicit Euler step + renormalisation)               */
   int self_term;    /* 1: keep the tensor's self offset K(0,0,0) = -I/3 (default);

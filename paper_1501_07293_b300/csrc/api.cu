@@ -65,6 +65,7 @@ static void free_ctx(mm_ctx* c) {
   cudaFree(c->m0); cudaFree(c->stA); cudaFree(c->stB); cudaFree(c->acc); cudaFree(c->Hs);
   cudaFree(c->hmap); cudaFree(c->kumap); cudaFree(c->S); cudaFree(c->Kh); cudaFree(c->tw);
   cudaFree(c->red); cudaFree(c->red_out); cudaFree(c->dflag); cudaFree(c->prog);
+  cudaFree(c->Kt); cudaFree(c->Bdft);
   mm_adjoint_free(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->ev) cudaEventDestroy(c->ev);
@@ -98,8 +99,8 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double M
   mm_opts o;
   mm_default_opts(&o);
   if (opts) o = *opts;
-  if (o.precision != MM_FP32)
-    return mm_fail(nullptr, MM_EUNSUPPORTED, "precision mode %d is not implemented (MM_FP32 only)", o.precision);
+  if (o.precision != MM_FP32 && o.precision != MM_SPLIT_BF16 && o.precision != MM_SPLIT_FP16)
+    return mm_fail(nullptr, MM_EINVAL, "unknown precision mode %d", o.precision);
   if (o.integrator != MM_RK4 && o.integrator != MM_EULER)
     return mm_fail(nullptr, MM_EINVAL, "unknown integrator %d", o.integrator);
 
@@ -112,6 +113,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double M
   c->d.hx = c->d.px == 1 ? 1 : c->d.px / 2 + 1;
   c->d.hy = c->d.py == 1 ? 1 : c->d.py / 2 + 1;
   c->d.N = (long long)grid[0] * grid[1] * grid[2];
+  c->d.prec = o.precision;
   c->delta = delta; c->Ms = Ms; c->A = A; c->Ku = Ku; c->alpha = alpha; c->gamma = gamma;
   c->opts = o;
   c->stream = (cudaStream_t)o.stream;
@@ -158,6 +160,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double M
     goto fail;
   }
   rc = mm_build_kernel(c);
+  if (rc == MM_OK && c->d.prec != MM_FP32) rc = mm_build_split(c);
   if (rc != MM_OK) {
     snprintf(g_create_err, sizeof g_create_err, "%s", c->err);
     goto fail;

@@ -101,6 +101,7 @@ extern "C" int mm_batch_create(mm_batch** out, int nfilms, const int* grids, dou
   mm_default_opts(&o);
   if (opts) o = *opts;
   if (o.integrator != MM_RK4) return bfail(nullptr, MM_EUNSUPPORTED, "batches run RK4 only");
+  if (o.precision != MM_FP32) return bfail(nullptr, MM_EUNSUPPORTED, "batches run the FP32 path only");
   for (int f = 0; f < nfilms; ++f)
     if (grids[3 * f + 2] > 16)
       return bfail(nullptr, MM_EUNSUPPORTED, "film %d: nz = %d; batched films have nz <= 16", f, grids[3 * f + 2]);

@@ -27,6 +27,11 @@ struct Dims {
   int px, py;
   int hx, hy;
   long long N;  // nx*ny*nz
+  // split-precision z product (0: FP32 direct sum; MM_SPLIT_BF16 / MM_SPLIT_FP16:
+  // tensor-core DFT along z, zsplit.cuh) and its per-context operands
+  int prec;
+  const float* Kt;             // [hx][PZ/2 + 1][6][hy] tensor transformed along z as well
+  const unsigned char* Bdft;   // the two DFT matrices, hi and lo, canonical shared-memory layout
 };
 
 // Per-cell physics constants, float32, precomputed in double on the host.
@@ -102,6 +107,8 @@ struct mm_ctx {
   int red_blocks;
   int* dflag;                // device error flags: [0] non-finite state, [1] kernel wait timed out
   ProgState* prog;           // clock, field program and the drive values the stages read
+  float* Kt;                 // split precision: tensor transformed along z ([hx][PZ/2+1][6][hy])
+  unsigned char* Bdft;       // split precision: DFT operands (device)
   int prog_n;                // segments installed
   int cur;                   // Euler: 0 -> state in m0, 1 -> state in stA
   int s_valid;               // S holds the x transform of the current state
@@ -163,6 +170,10 @@ int mm_fail(mm_ctx* c, int code, const char* fmt, ...);
 
 // setup.cu: build Kh (FP64 tensor, FP64 2D transform, FP32 store) and the twiddles.
 int mm_build_kernel(mm_ctx* c);
+// setup.cu: the split-precision operands Kt and Bdft (allocated and built; d.Kt, d.Bdft set)
+int mm_build_split(mm_ctx* c);
+// field.cu: padded z size (power of two >= nz) the z product works with
+int mm_nzm(int nz);
 
 // Same set-up into caller-provided buffers (Kc: 6 nz px py double2 scratch); returns kernels launched or < 0.
 int mm_setup_kernel_into(const Dims& d, int self_term, double2* Kc, float* Kh, cudaStream_t s);

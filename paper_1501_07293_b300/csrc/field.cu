@@ -25,6 +25,7 @@
 #include "fft.cuh"
 #include "bulk.cuh"
 #include "program.cuh"
+#include "zsplit.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -289,7 +290,10 @@ struct YzLayout {
   static constexpr int RS = PY + (PADS ? PY / 16 : 0) + 2;   // even: rows stay 16-byte aligned
 };
 
-template <int PY, int NZM>
+// Split-precision variants (PREC = MM_SPLIT_BF16 / MM_SPLIT_FP16) replace the
+// FP32 direct sum of step 3 by zs::zprod_split on the tensor cores; the DFT
+// operands follow the rows in shared memory.
+template <int PY, int NZM, int PREC = 0>
 __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __restrict__ Kh,
                                         const float2* __restrict__ twY, const Dims& d, int* flag, int kx,
                                         const Tick& tk = Tick{}) {
@@ -321,8 +325,10 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   {
     // the column's slice of the transformed tensor is first read by the z
     // product, after the transforms: start bringing it into L2 now
-    const char* kc = reinterpret_cast<const char*>(Kh + (long long)kx * d.hy * 6 * nz);
-    const int nlines = (d.hy * 6 * nz * (int)sizeof(float) + 127) >> 7;
+    const char* kc = PREC ? reinterpret_cast<const char*>(d.Kt + (long long)kx * d.hy * (NZM + 1) * 6)
+                          : reinterpret_cast<const char*>(Kh + (long long)kx * d.hy * 6 * nz);
+    const int bytes = PREC ? d.hy * (NZM + 1) * 6 * (int)sizeof(float) : d.hy * 6 * nz * (int)sizeof(float);
+    const int nlines = (bytes + 127) >> 7;
     for (int i = threadIdx.x; i < nlines; i += blockDim.x) prefetch_l2(kc + ((long long)i << 7));
   }
   // first y/z pass of a step: the last warp of CTA 0 advances the field
@@ -344,7 +350,36 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
     __syncthreads();
   }
   // Product of eq. 14 along z (see zprod).
-  if constexpr (NZM > 16)
+  if constexpr (PREC != 0) {
+    static_assert(NZM == 8 || NZM == 16, "split z product: 8 or 16 planes");
+    static_assert(PY >= 128 && PY % 128 == 0, "split z product: chunks of 128 ky");
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tbase;
+    unsigned char* Bsm = reinterpret_cast<unsigned char*>(buf + 3 * nz * RS);
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(d.Bdft);
+      uint4* dst = reinterpret_cast<uint4*>(Bsm);
+      for (int i = threadIdx.x; i < zs::Dft<NZM>::bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    if (threadIdx.x == 0) {
+      mbar_init(&mbar, 1);
+      mbar_fence_init();
+    }
+    if ((threadIdx.x >> 5) == 0) zs::tmem_alloc(&tbase, 512);
+    fence_proxy_async_smem();   // the DFT operands are read by the tensor cores (async proxy)
+    zs::fence_before();
+    __syncthreads();
+    zs::fence_after();
+    const uint32_t tb = tbase;
+    uint32_t phase = 0;
+    const bool ok = zs::zprod_split<PY, NZM, PREC, PADS>(buf, RS, nz, PY, d.hy, d.Kt + (long long)kx * d.hy * (NZM + 1) * 6,
+                                                         Bsm, tb, &mbar, phase, flag);
+    if (!ok) mbar_wait_bounded(&mbar, phase);   // MMAs still in flight get one more bounded wait
+    zs::fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) zs::tmem_dealloc(tb, 512);
+    if (!ok) return;
+  } else if constexpr (NZM > 16)
     zprod_column_chunked<NZM, (PY > 1 ? PADS : 0)>(buf, RS, PY, nz, Kh + (long long)kx * d.hy * 6 * nz, PY,
                                                    KyIdentity());
   else if (PY > 1)
@@ -369,10 +404,10 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   }
 }
 
-template <int PY, int NZM>
+template <int PY, int NZM, int PREC>
 __global__ void __launch_bounds__(512, 1) k_yz(float2* __restrict__ S, const float* __restrict__ Kh,
                                                 const float2* __restrict__ twY, Dims d, int* flag, Tick tk) {
-  body_yz<PY, NZM>(S, Kh, twY, d, flag, blockIdx.x, tk);
+  body_yz<PY, NZM, PREC>(S, Kh, twY, d, flag, blockIdx.x, tk);
 }
 
 // ---------------------------------------------------------------------------
@@ -829,13 +864,18 @@ static int pow2_ceil(int v) {
 }
 
 static int nzm_of(int nz) { return pow2_ceil(nz); }
+int mm_nzm(int nz) { return nzm_of(nz); }
 
 static int xtile(int half) { return half <= 256 ? 16 : (half <= 512 ? 8 : 4); }
 static int x_tile(int half) { return half <= 256 ? 8 : (half <= 512 ? 4 : 2); }
 static int x_rs(int half) { return half + (half + 1) / 16 + 2; }
 
 static int yz_rs(int py) { return py + (py >= 32 ? py / 16 : 0) + 2; }
-static size_t yz_smem(const Dims& d) { return sizeof(float2) * ((size_t)d.py + 3ull * d.nz * yz_rs(d.py)); }
+static size_t yz_smem(const Dims& d) {
+  size_t b = sizeof(float2) * ((size_t)d.py + 3ull * d.nz * yz_rs(d.py));
+  if (d.prec) b += mm_nzm(d.nz) == 8 ? zs::Dft<8>::bytes : zs::Dft<16>::bytes;
+  return b;
+}
 static size_t x_smem(int half) {
   return half == 0 ? 0 : sizeof(float2) * ((size_t)2 * half + 3ull * x_tile(half) * x_rs(half));
 }
@@ -863,6 +903,12 @@ int mm_supported(const Dims& d, char* why, int nwhy) {
   if (d.nz > 64) {
     snprintf(why, nwhy, "nz = %d > 64 is not supported by the z Toeplitz product of this build", d.nz);
     return 0;
+  }
+  if (d.prec) {
+    if (d.nz < 5 || d.nz > 16 || d.py < 128) {
+      snprintf(why, nwhy, "split precision needs 5 <= nz <= 16 and ny >= 33 (grid %d x %d x %d)", d.nx, d.ny, d.nz);
+      return 0;
+    }
   }
   const size_t need = yz_smem(d);
   if (need + 64 > kMaxSmem) {   // 64 bytes of static shared memory (the copy barrier)
@@ -945,9 +991,23 @@ static cudaError_t dispatch_x(const Dims& d, const Phys& ph, const StageArgs& a,
 template <int PY, int NZM>
 static cudaError_t run_yz_t(const Dims& d, const float2* tw, float2* S, const float* Kh, int* flag, const Tick& tk,
                             cudaStream_t s) {
+  if constexpr (PY >= 128 && (NZM == 8 || NZM == 16)) {
+    if (d.prec == MM_SPLIT_BF16 || d.prec == MM_SPLIT_FP16) {
+      static bool attr1 = false, attr2 = false;
+      if (d.prec == MM_SPLIT_BF16) {
+        if (cudaError_t e = allow_max_smem(k_yz<PY, NZM, MM_SPLIT_BF16>, attr1)) return e;
+        k_yz<PY, NZM, MM_SPLIT_BF16><<<d.hx, 512, yz_smem(d), s>>>(S, Kh, tw + PY, d, flag, tk);
+      } else {
+        if (cudaError_t e = allow_max_smem(k_yz<PY, NZM, MM_SPLIT_FP16>, attr2)) return e;
+        k_yz<PY, NZM, MM_SPLIT_FP16><<<d.hx, 512, yz_smem(d), s>>>(S, Kh, tw + PY, d, flag, tk);
+      }
+      return cudaGetLastError();
+    }
+  }
+  if (d.prec) return cudaErrorInvalidValue;
   static bool attr = false;
-  if (cudaError_t e = allow_max_smem(k_yz<PY, NZM>, attr)) return e;
-  k_yz<PY, NZM><<<d.hx, 512, yz_smem(d), s>>>(S, Kh, tw + PY, d, flag, tk);
+  if (cudaError_t e = allow_max_smem(k_yz<PY, NZM, 0>, attr)) return e;
+  k_yz<PY, NZM, 0><<<d.hx, 512, yz_smem(d), s>>>(S, Kh, tw + PY, d, flag, tk);
   return cudaGetLastError();
 }
 

@@ -66,6 +66,7 @@ extern "C" int mm_heff_noalloc(const int grid[3], double delta, double Ms, doubl
     return noalloc_fail(MM_EINVAL, "mm_heff_noalloc: bad term mask 0x%x", term_mask);
 
   Dims d;
+  memset(&d, 0, sizeof d);
   d.nx = grid[0]; d.ny = grid[1]; d.nz = grid[2];
   d.px = d.nx == 1 ? 1 : pow2_ge(2 * d.nx - 1);
   d.py = d.ny == 1 ? 1 : pow2_ge(2 * d.ny - 1);

@@ -18,6 +18,9 @@
 
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 __device__ __forceinline__ double log_z_plus_r(double x, double y, double z) {
@@ -197,4 +200,109 @@ int mm_setup_kernel_into(const Dims& d, int self_term, double2* Kc, float* Kh, c
   k_extract<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Kc, Kh, d);
   if (cudaGetLastError() != cudaSuccess) return -1;
   return n + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Split-precision operands (zsplit.cuh).
+// Kt[kx][kz][pair][ky], kz = 0 .. PZ/2 (ky fastest, so the lanes of a warp,
+// which hold consecutive ky, read consecutive words): the x/y-transformed tensor Kh
+// transformed along z with a length-PZ DFT of its offsets -(nz-1) .. nz-1,
+// scaled by 1/PZ.  Pairs even in z (xx yy zz xy) give the cosine sum
+// K(0) + 2 sum_d K(d) cos(2 pi kz d / PZ); pairs odd in z (xz yz, stored as
+// the imaginary part of their x/y transform, acting as i Kt) give
+// 2 sum_d K(d) sin(2 pi kz d / PZ), the real factor left after i (-2i) = 2.
+// FP64 arithmetic on the FP32 Kh values.
+// ---------------------------------------------------------------------------
+__global__ void k_ktz(const float* __restrict__ Kh, float* __restrict__ Kt, Dims d, int PZ) {
+  const int nkz = PZ / 2 + 1;
+  const long long total = (long long)d.hx * d.hy * nkz;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int ky = (int)(idx % d.hy);
+  const int kz = (int)((idx / d.hy) % nkz);
+  const int kx = (int)(idx / ((long long)d.hy * nkz));
+  const long long col = (long long)kx * d.hy + ky;
+  for (int p = 0; p < 6; ++p) {
+    const float* k = Kh + (col * 6 + p) * d.nz;
+    double s;
+    if (p < 4) {
+      s = k[0];
+      for (int dz = 1; dz < d.nz; ++dz) s += 2.0 * k[dz] * cospi(2.0 * kz * dz / PZ);
+    } else {
+      s = 0.0;
+      for (int dz = 1; dz < d.nz; ++dz) s += 2.0 * k[dz] * sinpi(2.0 * kz * dz / PZ);
+    }
+    Kt[(((long long)kx * nkz + kz) * 6 + p) * d.hy + ky] = (float)(s / PZ);
+  }
+}
+
+// hi/lo parts of v in the 16-bit type of the split (1: bfloat16, 2: float16)
+static void split16(double v, int prec, uint16_t* hi, uint16_t* lo) {
+  if (prec == MM_SPLIT_BF16) {
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+    const __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+    memcpy(hi, &h, 2);
+    memcpy(lo, &l, 2);
+  } else {
+    const __half h = __float2half_rn((float)v);
+    const __half l = __float2half_rn((float)(v - (double)__half2float(h)));
+    memcpy(hi, &h, 2);
+    memcpy(lo, &l, 2);
+  }
+}
+
+// byte offset of element (n, k) of an N x K operand in the canonical
+// no-swizzle K-major layout (core matrices of 8 rows x 16 bytes)
+static size_t canon(int n, int k, int N) { return ((size_t)(k / 8) * (N / 8) + n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2; }
+
+int mm_build_split(mm_ctx* c) {
+  Dims& d = c->d;
+  const int NZ = mm_nzm(d.nz), PZ = 2 * NZ;
+  const long long nkt = (long long)d.hx * d.hy * (PZ / 2 + 1) * 6;
+  if (cudaMalloc(&c->Kt, sizeof(float) * nkt) != cudaSuccess) {
+    cudaGetLastError();
+    return mm_fail(c, MM_ENOMEM, "split precision: cannot allocate the z-transformed tensor");
+  }
+  // GEMM 1 operand B1 (2 PZ x 2 NZ): rows re kz | im kz, columns re z | im z of
+  //   sum_z m(z) e^{-2 pi i kz z / PZ}:  re = sum re cos + im sin,  im = sum im cos - re sin
+  // GEMM 2 operand B2 (2 NZ x 2 PZ): rows re z | im z, columns re kz | im kz of
+  //   sum_kz h(kz) e^{+2 pi i kz z / PZ}: re = sum re cos - im sin,  im = sum re sin + im cos
+  const int N1 = 2 * PZ, K1 = 2 * NZ, N2 = 2 * NZ, K2 = 2 * PZ;
+  const size_t B1 = (size_t)N1 * K1 * 2, B2 = (size_t)N2 * K2 * 2;
+  std::vector<unsigned char> h(2 * B1 + 2 * B2, 0);
+  auto put = [&](size_t base_hi, size_t base_lo, int n, int k, int N, double v) {
+    uint16_t hi, lo;
+    split16(v, d.prec, &hi, &lo);
+    memcpy(&h[base_hi + canon(n, k, N)], &hi, 2);
+    memcpy(&h[base_lo + canon(n, k, N)], &lo, 2);
+  };
+  for (int n = 0; n < N1; ++n)
+    for (int k = 0; k < K1; ++k) {
+      const int kz = n % PZ, z = k % NZ;
+      const double th = 2.0 * MM_PI * kz * z / PZ;
+      const bool out_im = n >= PZ, in_im = k >= NZ;
+      const double v = !out_im ? (!in_im ? cos(th) : sin(th)) : (!in_im ? -sin(th) : cos(th));
+      put(0, B1, n, k, N1, v);
+    }
+  for (int n = 0; n < N2; ++n)
+    for (int k = 0; k < K2; ++k) {
+      const int z = n % NZ, kz = k % PZ;
+      const double th = 2.0 * MM_PI * kz * z / PZ;
+      const bool out_im = n >= NZ, in_im = k >= PZ;
+      const double v = !out_im ? (!in_im ? cos(th) : -sin(th)) : (!in_im ? sin(th) : cos(th));
+      put(2 * B1, 2 * B1 + B2, n, k, N2, v);
+    }
+  if (cudaMalloc(&c->Bdft, h.size()) != cudaSuccess) {
+    cudaGetLastError();
+    return mm_fail(c, MM_ENOMEM, "split precision: cannot allocate the DFT operands");
+  }
+  MM_CK(c, cudaMemcpy(c->Bdft, h.data(), h.size(), cudaMemcpyHostToDevice));
+  const long long tot = (long long)d.hx * d.hy * (PZ / 2 + 1);
+  k_ktz<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(c->Kh, c->Kt, d, PZ);
+  MM_CK(c, cudaGetLastError());
+  c->launches++;
+  MM_CK(c, cudaStreamSynchronize(c->stream));
+  d.Kt = c->Kt;
+  d.Bdft = c->Bdft;
+  return MM_OK;
 }

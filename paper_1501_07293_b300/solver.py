@@ -114,7 +114,8 @@ class Solver:
     """One film on one GPU: owns an mm_ctx."""
 
     def __init__(self, grid: Sequence[int], delta: float, Ms: float, A: float, Ku: float, alpha: float,
-                 gamma: float, integrator: str = "rk4", self_term: bool = True, device=None, stream=None):
+                 gamma: float, integrator: str = "rk4", self_term: bool = True, device=None, stream=None,
+                 precision: str = "fp32"):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
@@ -126,6 +127,7 @@ class Solver:
         L.mm_default_opts(ctypes.byref(o))
         o.integrator = MM_EULER if integrator == "euler" else MM_RK4
         o.self_term = 1 if self_term else 0
+        o.precision = {"fp32": MM_FP32, "split_bf16": MM_SPLIT_BF16, "split_fp16": MM_SPLIT_FP16}[precision]
         with torch.cuda.device(self.device):
             s = torch.cuda.current_stream() if stream is None else stream
             o.stream = s.cuda_stream
@@ -305,7 +307,7 @@ class _FilmView(Solver):
 class Batch:
     """Independent films of uneven size advanced together (mm_batch_*)."""
 
-    def __init__(self, grids, delta, Ms, A, Ku, alpha, gamma, device=None, stream=None):
+    def __init__(self, grids, delta, Ms, A, Ku, alpha, gamma, device=None, stream=None, precision: str = "fp32"):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
@@ -314,6 +316,7 @@ class Batch:
         L = lib()
         o = Opts()
         L.mm_default_opts(ctypes.byref(o))
+        o.precision = {"fp32": MM_FP32, "split_bf16": MM_SPLIT_BF16, "split_fp16": MM_SPLIT_FP16}[precision]
         with torch.cuda.device(self.device):
             s = torch.cuda.current_stream() if stream is None else stream
             o.stream = s.cuda_stream
