@@ -312,6 +312,74 @@ def bench_sp4(args, sample_every=1000):
     return out
 
 
+def bench_split(args, fp32_ms, steps=30, warmup=3):
+    """The split-precision forms (tensor-core z DFT with BF16 / FP16 hi+lo operands):
+    RK4 step time at 256x256x16 under the main protocol, the effective field's
+    relative L2 distance from the FP32 path, and the precision study (512x512x8
+    vortex, RK4): along 20 FP32 steps, the split field's distance from the FP32
+    field at every step's state."""
+    import torch
+    from paper_1501_07293_b300 import inputs
+    from paper_1501_07293_b300.solver import Solver
+    w = inputs.film_256x256x16()
+    mat = w.mat
+    m0 = torch.from_numpy(inputs.workload_state(w)).cuda()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    ref = Solver(w.grid, w.delta, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma)
+    ref.set_field(w.b_ext)
+    ref.set_m(m0)
+    H32 = ref.heff(15).double()
+    ref.close()
+    out = {"workload": w.name, "fp32_ms_per_step": fp32_ms}
+    for prec in ("split_bf16", "split_fp16"):
+        s = Solver(w.grid, w.delta, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma, precision=prec)
+        s.set_field(w.b_ext)
+        s.set_m(m0)
+        H = s.heff(15).double()
+        err = float(torch.linalg.norm(H - H32) / torch.linalg.norm(H32))
+        s.set_m(m0)
+        for _ in range(warmup):
+            flush.zero_()
+            s.step(1, w.dt)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            s.step(1, w.dt)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        kt = s.step_timed(5, w.dt)
+        out[prec] = {"ms_per_step": ms, "value": w.ncells / (ms * 1e-3), "unit": UNIT,
+                     "speedup_vs_fp32": fp32_ms / ms, "yz_ms_per_launch": kt[1] / 20,
+                     "heff_rel_l2_vs_fp32": err}
+        s.close()
+    # precision study
+    w3 = inputs.film_512x512x8()
+    m3 = torch.from_numpy(inputs.workload_state(w3)).cuda()
+    f32 = Solver(w3.grid, w3.delta, w3.mat.Ms, w3.mat.A, w3.mat.Ku, w3.mat.alpha, w3.mat.gamma)
+    sp = {p: Solver(w3.grid, w3.delta, w3.mat.Ms, w3.mat.A, w3.mat.Ku, w3.mat.alpha, w3.mat.gamma, precision=p)
+          for p in ("split_bf16", "split_fp16")}
+    f32.set_m(m3)
+    errs = {p: [] for p in sp}
+    for step in range(20):
+        state = f32.get_m()
+        Hr = f32.heff(15).double()
+        f32.set_m(state)
+        for p, sv in sp.items():
+            sv.set_m(state)
+            errs[p].append(float(torch.linalg.norm(sv.heff(15).double() - Hr) / torch.linalg.norm(Hr)))
+        f32.step(1, w3.dt)
+    out["precision_study_512x512x8"] = {p: {"max_heff_rel_l2": max(e), "mean_heff_rel_l2": sum(e) / len(e)}
+                                        for p, e in errs.items()}
+    f32.close()
+    for sv in sp.values():
+        sv.close()
+    return out
+
+
 TABLE1_GPU_SINGLE_MS = {8: 22.58, 16: 23.97, 32: 26.89, 64: 76.24}   # the paper's Table 1 (GTX 650 Ti)
 
 
@@ -445,6 +513,7 @@ def b300_arm(args, w):
         extra["adjoint"] = bench_adjoint(args)
         extra["sp4_protocol"] = bench_sp4(args)
         extra["sp3_table1"] = bench_sp3(args)
+        extra["split_precision"] = bench_split(args, 1e3 * t_max / K)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -322,6 +322,21 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
     for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) buf[(i / ny) * RS + i % ny] = Sk[i];
   }
   for (int i = threadIdx.x; i < PY; i += blockDim.x) tws[i] = twY[i];
+  // split precision: the DFT operands, the MMA barrier and the tensor memory,
+  // set up while the column's copies are in flight
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tbase;
+  unsigned char* Bsm = reinterpret_cast<unsigned char*>(buf + 3 * nz * RS);
+  if constexpr (PREC != 0) {
+    const uint4* src = reinterpret_cast<const uint4*>(d.Bdft);
+    uint4* dst = reinterpret_cast<uint4*>(Bsm);
+    for (int i = threadIdx.x; i < zs::Dft<NZM>::bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    if (threadIdx.x == 0) {
+      mbar_init(&mbar, 1);
+      mbar_fence_init();
+    }
+    if ((threadIdx.x >> 5) == 0) zs::tmem_alloc(&tbase, 512);
+  }
   {
     // the column's slice of the transformed tensor is first read by the z
     // product, after the transforms: start bringing it into L2 now
@@ -335,12 +350,20 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   // program's clock and writes the drive slots while the copies land (the x
   // kernels that follow read them; nothing in this kernel does)
   if (tk.p && kx == 0 && threadIdx.x >= blockDim.x - 32) prog_tick(tk);
-  if (bulk && !mbar_wait_bounded(&bar, 0)) {
+  const bool arrived = !bulk || mbar_wait_bounded(&bar, 0);
+  if constexpr (PREC != 0) {
+    fence_proxy_async_smem();   // the DFT operands are read by the tensor cores (async proxy)
+    zs::fence_before();
+  }
+  if (!__syncthreads_and(arrived)) {   // uniform: every thread leaves, tensor memory is freed
     if (threadIdx.x == 0) atomicOr(flag + 1, 1);
-    mbar_wait_bounded(&bar, 0);   // give copies in flight one more bounded chance before leaving
+    if (bulk) mbar_wait_bounded(&bar, 0);   // copies in flight get one more bounded chance
+    if constexpr (PREC != 0) {
+      if ((threadIdx.x >> 5) == 0) zs::tmem_dealloc(tbase, 512);
+    }
     return;
   }
-  __syncthreads();
+  if constexpr (PREC != 0) zs::fence_after();
   const int lane = threadIdx.x & 31;
   const int team = threadIdx.x / T, t = threadIdx.x % T, nteams = blockDim.x / T;
   const unsigned mask = team_mask<T>(lane);
@@ -353,23 +376,6 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   if constexpr (PREC != 0) {
     static_assert(NZM == 8 || NZM == 16, "split z product: 8 or 16 planes");
     static_assert(PY >= 128 && PY % 128 == 0, "split z product: chunks of 128 ky");
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ uint32_t tbase;
-    unsigned char* Bsm = reinterpret_cast<unsigned char*>(buf + 3 * nz * RS);
-    {
-      const uint4* src = reinterpret_cast<const uint4*>(d.Bdft);
-      uint4* dst = reinterpret_cast<uint4*>(Bsm);
-      for (int i = threadIdx.x; i < zs::Dft<NZM>::bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
-    }
-    if (threadIdx.x == 0) {
-      mbar_init(&mbar, 1);
-      mbar_fence_init();
-    }
-    if ((threadIdx.x >> 5) == 0) zs::tmem_alloc(&tbase, 512);
-    fence_proxy_async_smem();   // the DFT operands are read by the tensor cores (async proxy)
-    zs::fence_before();
-    __syncthreads();
-    zs::fence_after();
     const uint32_t tb = tbase;
     uint32_t phase = 0;
     const bool ok = zs::zprod_split<PY, NZM, PREC, PADS>(buf, RS, nz, PY, d.hy, d.Kt + (long long)kx * d.hy * (NZM + 1) * 6,
