@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--workload", default="film_256x256x16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-sweep and adjoint measurements")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16", "split_fp16"],
+                    help="the z product of the timed steps: FP32 direct sum or the tensor-core split forms")
     ap.add_argument("--ref-max-steps", type=int, default=8,
                     help="reference arm: at most this many oracle RK4 steps are executed and timed")
     return ap.parse_args()
@@ -424,7 +426,7 @@ def b300_arm(args, w):
     from paper_1501_07293_b300.solver import Solver
 
     mat = w.mat
-    s = Solver(w.grid, w.delta, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma)
+    s = Solver(w.grid, w.delta, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma, precision=args.precision)
     s.set_field(w.b_ext)
     m0 = inputs.workload_state(w)
     m0_dev = torch.from_numpy(m0).cuda()
@@ -528,7 +530,7 @@ def b300_arm(args, w):
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "grid": list(w.grid), "delta_m": w.delta, "integrator": "rk4",
-                       "dt_s": w.dt, "variant": "fp32",
+                       "dt_s": w.dt, "variant": args.precision,
                        "l2": "flushed between timed steps (512 MiB write outside the events)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "kernel": kernels[dom], "achieved": achieved, "peak": peak,
