@@ -382,6 +382,47 @@ def bench_split(args, fp32_ms, steps=30, warmup=3):
     return out
 
 
+def bench_cufft(args, ours_ms_per_stage, reps=20):
+    """Timed comparison only: the demagnetising convolution of one field evaluation as
+    a library pipeline -- cuFFT (through torch.fft) R2C of the three zero-padded
+    components on the px x py x 2nz grid, the 3x3 symmetric product with six
+    spectral tensor components, C2R of the three results -- against one stage of
+    our kernels (k_yz + k_x, which also do the exchange/anisotropy/Zeeman/LLG/RK4
+    work and the next x transform).  The tensor values do not change the cost,
+    so random spectra of the right shape stand in for them."""
+    import torch
+    from paper_1501_07293_b300 import inputs
+    w = inputs.film_256x256x16()
+    nx, ny, nz = w.grid
+    px, py, pz = 2 * nx, 2 * ny, 2 * nz
+    g = torch.Generator(device="cuda").manual_seed(7)
+    M = torch.zeros(3, px, py, pz, device="cuda")
+    M[:, :nx, :ny, :nz] = torch.randn(3, nx, ny, nz, device="cuda", generator=g)
+    K = torch.randn(6, px, py, pz // 2 + 1, device="cuda", generator=g)   # xx yy zz xy xz yz
+    pairs = [[0, 3, 4], [3, 1, 5], [4, 5, 2]]
+    stream = torch.cuda.current_stream()
+
+    def conv():
+        Mh = torch.fft.rfftn(M, dim=(1, 2, 3))
+        H = [sum(K[pairs[a][b]] * Mh[b] for b in range(3)) for a in range(3)]
+        return torch.fft.irfftn(torch.stack(H), s=(px, py, pz), dim=(1, 2, 3))[:, :nx, :ny, :nz]
+
+    for _ in range(3):
+        conv()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        conv()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": f"demag convolution of {w.name}, padded {px}x{py}x{pz}, cuFFT via torch.fft",
+            "cufft_pipeline_ms_per_field_eval": ms, "ours_ms_per_stage": ours_ms_per_stage,
+            "ours_speedup": ms / ours_ms_per_stage,
+            "note": "timed comparison only; not on any product path"}
+
+
 TABLE1_GPU_SINGLE_MS = {8: 22.58, 16: 23.97, 32: 26.89, 64: 76.24}   # the paper's Table 1 (GTX 650 Ti)
 
 
@@ -516,6 +557,7 @@ def b300_arm(args, w):
         extra["sp4_protocol"] = bench_sp4(args)
         extra["sp3_table1"] = bench_sp3(args)
         extra["split_precision"] = bench_split(args, 1e3 * t_max / K)
+        extra["cufft_comparison"] = bench_cufft(args, float(per_launch_ms["yz"] + per_launch_ms["x"]))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
