@@ -74,7 +74,11 @@ typedef struct {
                        (the paper's explicit Euler step + renormalisation)               */
   int self_term;    /* 1: keep the tensor's self offset K(0,0,0) = -I/3 (default);
                        0: drop it as the paper's tensor listing does                    */
-  int obs_every;    /* reserved (0)                                                      */
+  int obs_every;    /* > 0: every obs_every-th step since mm_set_m appends a record
+                       (t, step, <mx>, <my>, <mz>, max|dm/dt|) to a device ring of the
+                       last 65536 records, inside the step graph (no host round trip;
+                       one extra launch per step); read with mm_get_series.  The paper
+                       writes <m> every 1000 steps (script of Appendix A).  0: off.      */
   void* stream;     /* cudaStream_t the context enqueues on; NULL = legacy default       */
 } mm_opts;
 
@@ -234,6 +238,16 @@ int mm_step_timed(mm_ctx* ctx, int n, double dt, double ms_out[3]);
  */
 int mm_adjoint(mm_ctx* ctx, int n, double dt, int ckpt_every, const float* dL_dm_final,
                float* dL_dh, float* dL_dku, float* dL_dm0);
+
+/*
+ * Observables series (mm_opts.obs_every > 0): copies the most recent records
+ * written since mm_set_m, oldest first, at most max_records of them, into out
+ * (host, 6 doubles each: time (s), step, <mx>, <my>, <mz>, max over cells of
+ * |dm/dt| (rad/s) at the start of the recorded step); *n_records = how many.
+ * <m> is of the state after the step, accumulated in FP64.  Synchronises.
+ * MM_EINVAL when the context was created with obs_every = 0.
+ */
+int mm_get_series(mm_ctx* ctx, double* out, int max_records, int* n_records);
 
 /* Number of kernels this context has enqueued so far (graph nodes counted per replay). */
 long long mm_launch_count(const mm_ctx* ctx);

@@ -5,6 +5,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 static char g_create_err[512] = "";
@@ -65,7 +67,7 @@ static void free_ctx(mm_ctx* c) {
   cudaFree(c->m0); cudaFree(c->stA); cudaFree(c->stB); cudaFree(c->acc); cudaFree(c->Hs);
   cudaFree(c->hmap); cudaFree(c->kumap); cudaFree(c->S); cudaFree(c->Kh); cudaFree(c->tw);
   cudaFree(c->red); cudaFree(c->red_out); cudaFree(c->dflag); cudaFree(c->prog);
-  cudaFree(c->Kt); cudaFree(c->Bdft);
+  cudaFree(c->Kt); cudaFree(c->Bdft); cudaFree(c->series);
   mm_adjoint_free(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->ev) cudaEventDestroy(c->ev);
@@ -103,6 +105,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double M
     return mm_fail(nullptr, MM_EINVAL, "unknown precision mode %d", o.precision);
   if (o.integrator != MM_RK4 && o.integrator != MM_EULER)
     return mm_fail(nullptr, MM_EINVAL, "unknown integrator %d", o.integrator);
+  if (o.obs_every < 0) return mm_fail(nullptr, MM_EINVAL, "obs_every = %d < 0", o.obs_every);
 
   int rc = MM_OK;
   mm_ctx* c = (mm_ctx*)calloc(1, sizeof(mm_ctx));
@@ -144,6 +147,10 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double M
     ALLOC(c->red_out, sizeof(double) * 16);
     ALLOC(c->dflag, sizeof(int) * 4);
     ALLOC(c->prog, sizeof(ProgState));
+    if (o.obs_every > 0) {
+      c->series_cap = MM_SERIES_CAP;
+      ALLOC(c->series, sizeof(double) * 6 * (size_t)c->series_cap);
+    }
   }
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) {
@@ -152,6 +159,10 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double M
     goto fail;
   }
   if (cudaMemsetAsync(c->dflag, 0, sizeof(int) * 4, c->stream) != cudaSuccess) {
+    rc = mm_fail(nullptr, MM_ECUDA, "memset failed");
+    goto fail;
+  }
+  if (c->series && cudaMemsetAsync(c->series, 0, sizeof(double) * 6 * (size_t)c->series_cap, c->stream) != cudaSuccess) {
     rc = mm_fail(nullptr, MM_ECUDA, "memset failed");
     goto fail;
   }
@@ -207,6 +218,9 @@ extern "C" int mm_set_m(mm_ctx* c, const float* m) {
   if (launch_normalise(c->d, c->m0, c->dflag, c->stream) < 0) return mm_fail(c, MM_ECUDA, "normalise launch failed");
   c->launches++;
   c->steps = 0;
+  // the step count (and the observables series) restarts with the new state
+  MM_CK(c, cudaMemsetAsync(&c->prog->nstep, 0, sizeof(long long), c->stream));
+  if (c->series) MM_CK(c, cudaMemsetAsync(c->series, 0, sizeof(double) * 6 * (size_t)c->series_cap, c->stream));
   return MM_OK;
 }
 
@@ -307,9 +321,14 @@ static int enqueue_step(mm_ctx* c, cudaStream_t s, double dt, int from, long lon
     a.m_in = from ? c->stA : c->m0;
     a.m_out = from ? c->m0 : c->stA;
     stage_drive(c, a, 0, dt);
+    if (c->series) a.maxdmdt = &c->prog->maxdmdt;
     const int k = launch_stage(c->d, ph, a, c->tw, c->S, c->Kh, c->dflag, s);
     if (k < 0) return k;
     *nk += k;
+    if (c->series) {
+      if (launch_record(c, a.m_out, s) < 0) return -4;
+      *nk += 1;
+    }
     return 0;
   }
   a.mode = 1;
@@ -322,9 +341,14 @@ static int enqueue_step(mm_ctx* c, cudaStream_t s, double dt, int from, long lon
     a.m_in = in[s4];
     a.m_out = outp[s4];
     stage_drive(c, a, s4, dt);
+    a.maxdmdt = (c->series && s4 == 0) ? &c->prog->maxdmdt : nullptr;
     const int k = launch_stage(c->d, ph, a, c->tw, c->S, c->Kh, c->dflag, s);
     if (k < 0) return k;
     *nk += k;
+  }
+  if (c->series) {
+    if (launch_record(c, c->m0, s) < 0) return -4;
+    *nk += 1;
   }
   return 0;
 }
@@ -573,5 +597,28 @@ extern "C" int mm_selftest_wait_timeout(mm_ctx* c, unsigned polls) {
   k_wait_selftest<<<1, 32, 0, c->stream>>>(c->dflag, polls);
   if (cudaGetLastError() != cudaSuccess) return mm_fail(c, MM_ECUDA, "self-test launch failed");
   c->launches++;
+  return MM_OK;
+}
+
+extern "C" int mm_get_series(mm_ctx* c, double* out, int max_records, int* n_records) {
+  if (!c) return MM_EINVAL;
+  if (!n_records || (max_records > 0 && !out)) return mm_fail(c, MM_EINVAL, "mm_get_series: NULL output");
+  *n_records = 0;
+  if (!c->series) return mm_fail(c, MM_EINVAL, "mm_get_series: the context was created with obs_every = 0");
+  long long nstep = 0;
+  MM_CK(c, cudaMemcpyAsync(&nstep, &c->prog->nstep, sizeof nstep, cudaMemcpyDeviceToHost, c->stream));
+  MM_CK(c, cudaStreamSynchronize(c->stream));
+  const long long total = nstep / c->opts.obs_every;   // records written since mm_set_m
+  const long long avail = total < c->series_cap ? total : c->series_cap;
+  const long long n = avail < max_records ? avail : (max_records > 0 ? max_records : 0);
+  if (n == 0) return MM_OK;
+  std::vector<double> ring(6 * (size_t)c->series_cap);
+  MM_CK(c, cudaMemcpy(ring.data(), c->series, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost));
+  // the n most recent records, oldest first
+  for (long long i = 0; i < n; ++i) {
+    const long long rec = total - n + i;
+    memcpy(out + 6 * i, ring.data() + 6 * (rec % c->series_cap), 6 * sizeof(double));
+  }
+  *n_records = (int)n;
   return MM_OK;
 }

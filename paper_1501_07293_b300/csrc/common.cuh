@@ -20,6 +20,7 @@
 
 #define MM_PI 3.14159265358979323846
 #define MM_MU0 (4.0e-7 * MM_PI)
+#define MM_SERIES_CAP 65536   // records kept by the observables ring (obs_every > 0)
 
 // Grid and launch geometry of one film, passed by value to kernels.
 struct Dims {
@@ -57,7 +58,9 @@ struct ProgSeg {
 };
 struct ProgState {
   double clock;         // context time (s) of the current state
-  int nseg, pad;
+  long long nstep;      // steps taken since mm_set_m (advanced with the clock)
+  float maxdmdt;        // obs_every > 0: max |dm/dt| at the start of the step under way (atomic max of the bits)
+  int nseg;
   float base[8];        // bx, by, bz, g1, g2 outside every segment
   float drive[5][8];    // bx, by, bz, g1, g2 at RK4 stages 0..3 of the step under way; [4] at `clock`
   ProgSeg seg[MM_PROGRAM_MAX];
@@ -107,6 +110,8 @@ struct mm_ctx {
   int red_blocks;
   int* dflag;                // device error flags: [0] non-finite state, [1] kernel wait timed out
   ProgState* prog;           // clock, field program and the drive values the stages read
+  double* series;            // obs_every > 0: ring of records (t, step, <mx>, <my>, <mz>, max|dm/dt|)
+  int series_cap;            // records in the ring
   float* Kt;                 // split precision: tensor transformed along z ([hx][PZ/2+1][6][hy])
   unsigned char* Bdft;       // split precision: DFT operands (device)
   int prog_n;                // segments installed
@@ -135,6 +140,7 @@ Phys mm_make_phys(const mm_ctx* c);
 
 // program.cu: stream-ordered writes of the program state (1 launch each)
 int mm_prog_init(mm_ctx* c);        // clock 0, no segments, base and every drive slot from mm_make_phys
+int launch_record(mm_ctx* c, const float* m, cudaStream_t s);   // observables record of the new state (1 launch)
 int mm_prog_push_base(mm_ctx* c);   // base <- mm_make_phys (b_ext, alpha); drive slots refreshed at the clock
 
 // One film of a batch, as the batched kernels see it (device array).

@@ -20,6 +20,8 @@ __device__ void refresh_now(ProgState* p) { prog_eval(p, p->clock, p->drive[4]);
 __global__ void k_prog_init(ProgState* p, Phys ph) {
   if (threadIdx.x != 0) return;
   p->clock = 0.0;
+  p->nstep = 0;
+  p->maxdmdt = 0.f;
   p->nseg = 0;
   const float b[5] = {ph.bx, ph.by, ph.bz, ph.g1, ph.g2};
   for (int c = 0; c < 8; ++c) p->base[c] = c < 5 ? b[c] : 0.f;
@@ -59,6 +61,55 @@ void g_of(double gamma, double alpha, float* g1, float* g2) {
 }
 
 }  // namespace
+
+// Observables record (obs_every > 0), one launch per step after the step's
+// kernels: on every obs_every-th step, <m> of the new state (FP64 block sums,
+// atomically added into a record the previous record zeroed), the clock, the
+// step count and max |dm/dt| at the step's start (recorded by its first stage);
+// max |dm/dt| is reset every step.  Off-cadence steps return at once.
+__global__ void __launch_bounds__(256) k_record(const float* __restrict__ m, long long N, ProgState* p,
+                                                double* series, int cap, int every) {
+  const long long n = p->nstep;
+  const bool rec_step = n > 0 && n % every == 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !rec_step) p->maxdmdt = 0.f;
+  if (!rec_step) return;
+  const long long rec = n / every - 1;
+  double* r = series + (rec % cap) * 6;
+  double s[3] = {0.0, 0.0, 0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    s[0] += m[i]; s[1] += m[i + N]; s[2] += m[i + 2 * N];
+  }
+  __shared__ double red[3][8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double v = s[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[c][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double v = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v += red[threadIdx.x][k];
+    atomicAdd(r + 2 + threadIdx.x, v / (double)N);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    r[0] = p->clock;
+    r[1] = (double)n;
+    r[5] = (double)p->maxdmdt;
+    p->maxdmdt = 0.f;
+    double* nx = series + ((rec + 1) % cap) * 6;   // the next record accumulates from zero
+    for (int k = 0; k < 6; ++k) nx[k] = 0.0;
+  }
+}
+
+int launch_record(mm_ctx* c, const float* m, cudaStream_t s) {
+  const long long N = c->d.N;
+  int nb = (int)((N + 255) / 256);
+  if (nb > 296) nb = 296;
+  k_record<<<nb, 256, 0, s>>>(m, N, c->prog, c->series, c->series_cap, c->opts.obs_every);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
 
 int mm_prog_init(mm_ctx* c) {
   k_prog_init<<<1, 32, 0, c->stream>>>(c->prog, mm_make_phys(c));

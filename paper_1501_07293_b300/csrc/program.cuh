@@ -36,5 +36,8 @@ static __device__ __noinline__ void prog_tick(const Tick tk) {
     prog_eval(p, t + c * tk.dt, p->drive[lane]);
   }
   __syncwarp();
-  if (lane == 0) p->clock = t + tk.dt;
+  if (lane == 0) {
+    p->clock = t + tk.dt;
+    p->nstep += 1;
+  }
 }

@@ -63,6 +63,7 @@ _SIGNATURES = {
     "mm_observables": (_I, [_P, ctypes.POINTER(_D)]),
     "mm_step_timed": (_I, [_P, _I, _D, ctypes.POINTER(_D)]),
     "mm_adjoint": (_I, [_P, _I, _D, _I, _P, _P, _P, _P]),
+    "mm_get_series": (_I, [_P, _P, _I, ctypes.POINTER(_I)]),
     "mm_launch_count": (ctypes.c_longlong, [_P]),
     "mm_sync": (_I, [_P]),
     "mm_selftest_wait_timeout": (_I, [_P, ctypes.c_uint]),
@@ -115,7 +116,7 @@ class Solver:
 
     def __init__(self, grid: Sequence[int], delta: float, Ms: float, A: float, Ku: float, alpha: float,
                  gamma: float, integrator: str = "rk4", self_term: bool = True, device=None, stream=None,
-                 precision: str = "fp32"):
+                 precision: str = "fp32", obs_every: int = 0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
@@ -128,6 +129,7 @@ class Solver:
         o.integrator = MM_EULER if integrator == "euler" else MM_RK4
         o.self_term = 1 if self_term else 0
         o.precision = {"fp32": MM_FP32, "split_bf16": MM_SPLIT_BF16, "split_fp16": MM_SPLIT_FP16}[precision]
+        o.obs_every = int(obs_every)
         with torch.cuda.device(self.device):
             s = torch.cuda.current_stream() if stream is None else stream
             o.stream = s.cuda_stream
@@ -205,6 +207,13 @@ class Solver:
 
     def set_time(self, t: float):
         self._check(self._L.mm_set_time(self.ctx, float(t)))
+
+    def series(self, max_records: int = 65536) -> np.ndarray:
+        """Observables records (obs_every > 0), oldest first: rows (t, step, <mx>, <my>, <mz>, max|dm/dt|)."""
+        buf = np.zeros((max_records, 6), dtype=np.float64)
+        n = _I(0)
+        self._check(self._L.mm_get_series(self.ctx, buf.ctypes.data, int(max_records), ctypes.byref(n)))
+        return buf[:n.value].copy()
 
     def time(self) -> float:
         """The context clock (s); synchronises."""
