@@ -434,7 +434,7 @@ def bench_sp3(args, steps=500, warmup=20):
     from paper_1501_07293_b300.solver import Solver
     stream = torch.cuda.current_stream()
     rows = []
-    for n in (8, 16, 32, 64):
+    for n in (8, 16, 32, 64, 128):
         w = inputs.sp3_cube(n)
         mat = w.mat
         s = Solver(w.grid, w.delta, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma, integrator="euler")
@@ -448,7 +448,7 @@ def bench_sp3(args, steps=500, warmup=20):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         rows.append({"n": n, "ms_per_step": ms, "cell_steps_per_s": n ** 3 / (ms * 1e-3),
-                     "paper_gtx650ti_single_ms": TABLE1_GPU_SINGLE_MS[n]})
+                     "paper_gtx650ti_single_ms": TABLE1_GPU_SINGLE_MS.get(n)})
         s.close()
     return {"workload": "muMAG standard problem 3 cube n^3, Euler, FP32, one field evaluation per step",
             "steps": steps, "rows": rows}

@@ -67,7 +67,7 @@ static void free_ctx(mm_ctx* c) {
   cudaFree(c->m0); cudaFree(c->stA); cudaFree(c->stB); cudaFree(c->acc); cudaFree(c->Hs);
   cudaFree(c->hmap); cudaFree(c->kumap); cudaFree(c->S); cudaFree(c->Kh); cudaFree(c->tw);
   cudaFree(c->red); cudaFree(c->red_out); cudaFree(c->dflag); cudaFree(c->prog);
-  cudaFree(c->Kt); cudaFree(c->Bdft); cudaFree(c->series);
+  cudaFree(c->Kt); cudaFree(c->Bdft); cudaFree(c->series); cudaFree(c->T);
   mm_adjoint_free(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->ev) cudaEventDestroy(c->ev);
@@ -147,6 +147,10 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double M
     ALLOC(c->red_out, sizeof(double) * 16);
     ALLOC(c->dflag, sizeof(int) * 4);
     ALLOC(c->prog, sizeof(ProgState));
+    if (!mm_yz_fused(c->d)) {   // the split y/z pass meets in a global buffer
+      ALLOC(c->T, sizeof(float2) * (size_t)c->d.hx * 3 * c->d.nz * c->d.py);
+      c->d.T = c->T;
+    }
     if (o.obs_every > 0) {
       c->series_cap = MM_SERIES_CAP;
       ALLOC(c->series, sizeof(double) * 6 * (size_t)c->series_cap);
@@ -479,11 +483,12 @@ extern "C" int mm_step_timed(mm_ctx* c, int n, double dt, double ms_out[3]) {
       a.m_out = outp[s4];
       stage_drive(c, a, s4, dt);
       for (int part = 1; part < 3; ++part) {
-        if (launch_field_part(c->d, ph, a, c->tw, c->S, c->Kh, c->dflag, c->stream, part) < 0) {
+        const int nl = launch_field_part(c->d, ph, a, c->tw, c->S, c->Kh, c->dflag, c->stream, part);
+        if (nl < 0) {
           rc = mm_fail(c, MM_ECUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
           break;
         }
-        c->launches++;
+        c->launches += nl;
         cls[ne - 1] = part;
         cudaEventRecord(ev[ne++], c->stream);
       }

@@ -118,6 +118,10 @@ extern "C" int mm_batch_create(mm_batch** out, int nfilms, const int* grids, dou
       return rc;
     }
     b->film.push_back(c);
+    if (!mm_yz_fused(c->d)) {
+      free_batch(b);
+      return bfail(nullptr, MM_EUNSUPPORTED, "film %d: its kx columns exceed one CTA (batched films need the fused y/z pass)", f);
+    }
   }
   if (cudaMalloc(&b->dev, sizeof(BatchFilm) * nfilms) != cudaSuccess ||
       cudaMalloc(&b->maxdmdt, sizeof(float) * nfilms) != cudaSuccess ||

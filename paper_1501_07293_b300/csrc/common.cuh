@@ -33,6 +33,7 @@ struct Dims {
   int prec;
   const float* Kt;             // [hx][PZ/2 + 1][6][hy] tensor transformed along z as well
   const unsigned char* Bdft;   // the two DFT matrices, hi and lo, canonical shared-memory layout
+  float2* T;                   // split y/z pass (columns beyond one CTA): [hx][3 nz][py] (else null)
 };
 
 // Per-cell physics constants, float32, precomputed in double on the host.
@@ -113,6 +114,7 @@ struct mm_ctx {
   double* series;            // obs_every > 0: ring of records (t, step, <mx>, <my>, <mz>, max|dm/dt|)
   int series_cap;            // records in the ring
   float* Kt;                 // split precision: tensor transformed along z ([hx][PZ/2+1][6][hy])
+  float2* T;                 // split y/z pass buffer (columns beyond one CTA's shared memory)
   unsigned char* Bdft;       // split precision: DFT operands (device)
   int prog_n;                // segments installed
   int cur;                   // Euler: 0 -> state in m0, 1 -> state in stA
@@ -180,6 +182,11 @@ int mm_build_kernel(mm_ctx* c);
 int mm_build_split(mm_ctx* c);
 // field.cu: padded z size (power of two >= nz) the z product works with
 int mm_nzm(int nz);
+// field.cu: 1 if one CTA holds a kx column (the fused y/z kernel), 0 if the
+// y/z pass runs as three kernels through d.T
+int mm_yz_fused(const Dims& d);
+// field.cu: kernels one y/z pass launches (1 fused, 3 split)
+int mm_yz_launches(const Dims& d);
 
 // Same set-up into caller-provided buffers (Kc: 6 nz px py double2 scratch); returns kernels launched or < 0.
 int mm_setup_kernel_into(const Dims& d, int self_term, double2* Kc, float* Kh, cudaStream_t s);

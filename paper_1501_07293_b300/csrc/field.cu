@@ -417,6 +417,82 @@ __global__ void __launch_bounds__(512, 1) k_yz(float2* __restrict__ S, const flo
 }
 
 // ---------------------------------------------------------------------------
+// Split y/z pass, for kx columns that do not fit one CTA's shared memory (more
+// than 64 planes, or 3 nz py complex values beyond 227 KB): the y transforms
+// and the z product meet in a global buffer T[kx][3 nz][py] (L2-resident at
+// the sizes it serves).
+//   k_yt<PY, DIR>: CTA = (kx, a group of rows, one team each).  DIR -1: rows of
+//                  S (ny values) -> forward transform -> T (py values);
+//                  DIR +1: T -> inverse transform -> S (first ny values).
+//   k_zt<NZM>:     CTA = (kx, KB consecutive ky): the 3 nz values of each ky
+//                  from T into shared memory, the z product, back to T.
+// ---------------------------------------------------------------------------
+template <int PY, int DIR>
+__global__ void __launch_bounds__(256) k_yt(float2* __restrict__ S, float2* __restrict__ T,
+                                            const float2* __restrict__ twY, Dims d, Tick tk) {
+  constexpr int TM = TeamOf<PY>::v;
+  constexpr int PADS = YzLayout<PY>::PADS;
+  constexpr int RS = YzLayout<PY>::RS;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* tws = sm;
+  float2* rows = sm + PY;
+  const int kx = blockIdx.x, ny = d.ny, NP = 3 * d.nz;
+  const int nrows = blockDim.x / TM;
+  const int r0 = blockIdx.y * nrows;
+  float2* Sk = S + (long long)kx * NP * ny;
+  float2* Tk = T + (long long)kx * NP * PY;
+  for (int i = threadIdx.x; i < PY; i += blockDim.x) tws[i] = twY[i];
+  const int nin = DIR < 0 ? ny : PY;
+  for (int i = threadIdx.x; i < nrows * nin; i += blockDim.x) {
+    const int r = i / nin, e = i % nin;
+    if (r0 + r >= NP) continue;
+    rows[r * RS + e] = DIR < 0 ? Sk[(long long)(r0 + r) * ny + e] : Tk[(long long)(r0 + r) * PY + e];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int team = threadIdx.x / TM, t = threadIdx.x % TM;
+  if (PY > 1 && r0 + team < NP)
+    team_fft_io<PY, TM, DIR, 1, 0, PADS, 0>(rows + team * RS, t, team_mask<TM>(lane), tws, nin, DIR < 0 ? PY : ny);
+  __syncthreads();
+  const int nout = DIR < 0 ? PY : ny;
+  for (int i = threadIdx.x; i < nrows * nout; i += blockDim.x) {
+    const int r = i / nout, e = i % nout;
+    if (r0 + r >= NP) continue;
+    if (DIR < 0) Tk[(long long)(r0 + r) * PY + e] = rows[r * RS + e];
+    else Sk[(long long)(r0 + r) * ny + e] = rows[r * RS + e];
+  }
+  // first y/z launch of a step: the field program's clock and drive slots
+  if (DIR < 0 && tk.p && kx == 0 && blockIdx.y == 0 && threadIdx.x < 32) prog_tick(tk);
+}
+
+struct KyShift {
+  int k0;
+  __device__ int operator()(int k) const { return k0 + k; }
+};
+
+template <int NZM>
+__global__ void __launch_bounds__(512, 1) k_zt(float2* __restrict__ T, const float* __restrict__ Kh, Dims d, int KB) {
+  extern __shared__ __align__(16) float2 zb[];   // [3 nz][KB]
+  const int kx = blockIdx.x, ky0 = blockIdx.y * KB;
+  const int nz = d.nz, NP = 3 * nz, py = d.py;
+  const int len = py - ky0 < KB ? py - ky0 : KB;
+  float2* Tk = T + (long long)kx * NP * py;
+  for (int i = threadIdx.x; i < NP * len; i += blockDim.x) {
+    const int p = i / len, j = i % len;
+    zb[p * KB + j] = Tk[(long long)p * py + ky0 + j];
+  }
+  __syncthreads();
+  const float* Kk = Kh + (long long)kx * d.hy * 6 * nz;
+  if constexpr (NZM > 16) zprod_column_chunked<NZM, 0>(zb, KB, len, nz, Kk, py, KyShift{ky0});
+  else zprod_column<NZM, 0>(zb, KB, len, nz, Kk, d.hy, py, KyShift{ky0});
+  __syncthreads();
+  for (int i = threadIdx.x; i < NP * len; i += blockDim.x) {
+    const int p = i / len, j = i % len;
+    Tk[(long long)p * py + ky0 + j] = zb[p * KB + j];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // per-cell field terms and LLG update
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
@@ -901,13 +977,24 @@ static cudaError_t allow_max_smem(K kernel, bool& done) {
   return e;
 }
 
+static const size_t kZtBudget = 200 * 1024;   // shared memory of one k_zt CTA (its ky block)
+
+static int zt_kb(const Dims& d) {
+  int kb = (int)(kZtBudget / (sizeof(float2) * 3ull * d.nz));
+  if (kb > 128) kb = 128;
+  return kb;
+}
+
+int mm_yz_fused(const Dims& d) { return nzm_of(d.nz) <= 64 && yz_smem(d) + 64 <= kMaxSmem; }
+int mm_yz_launches(const Dims& d) { return mm_yz_fused(d) ? 1 : 3; }
+
 int mm_supported(const Dims& d, char* why, int nwhy) {
   if (d.px > 2048 || d.py > 2048) {
     snprintf(why, nwhy, "padded size %dx%d exceeds 2048 (nx, ny <= 1024 supported)", d.px, d.py);
     return 0;
   }
-  if (d.nz > 64) {
-    snprintf(why, nwhy, "nz = %d > 64 is not supported by the z Toeplitz product of this build", d.nz);
+  if (d.nz > 128) {
+    snprintf(why, nwhy, "nz = %d > 128 is not supported by the z Toeplitz product of this build", d.nz);
     return 0;
   }
   if (d.prec) {
@@ -916,10 +1003,16 @@ int mm_supported(const Dims& d, char* why, int nwhy) {
       return 0;
     }
   }
-  const size_t need = yz_smem(d);
-  if (need + 64 > kMaxSmem) {   // 64 bytes of static shared memory (the copy barrier)
-    snprintf(why, nwhy, "one kx column (3 x nz x py = 3 x %d x %d complex) exceeds shared memory", d.nz, d.py);
-    return 0;
+  if (!mm_yz_fused(d)) {
+    // the split y/z pass: a ky block of the z product and a row group of the y transforms
+    if (d.prec) {
+      snprintf(why, nwhy, "split precision needs a kx column in one CTA (3 x %d x %d complex too large)", d.nz, d.py);
+      return 0;
+    }
+    if (zt_kb(d) < 8) {
+      snprintf(why, nwhy, "nz = %d: a block of 8 ky of the z product exceeds shared memory", d.nz);
+      return 0;
+    }
   }
   return 1;
 }
@@ -1045,8 +1138,73 @@ static cudaError_t run_yz_nz(const Dims& d, const float2* tw, float2* S, const f
 #undef MM_CALL_YZ
 }
 
+template <int PY>
+static cudaError_t run_yt(const Dims& d, const float2* tw, float2* S, int dir, const Tick& tk, cudaStream_t s) {
+  constexpr int TM = TeamOf<PY>::v;
+  const int threads = 256, nrows = threads / TM;
+  const size_t smem = sizeof(float2) * ((size_t)PY + (size_t)nrows * YzLayout<PY>::RS);
+  dim3 grid(d.hx, (3 * d.nz + nrows - 1) / nrows);
+  if (dir < 0) {
+    static bool attr = false;
+    if (cudaError_t e = allow_max_smem(k_yt<PY, -1>, attr)) return e;
+    k_yt<PY, -1><<<grid, threads, smem, s>>>(S, d.T, tw + PY, d, tk);
+  } else {
+    static bool attr = false;
+    if (cudaError_t e = allow_max_smem(k_yt<PY, 1>, attr)) return e;
+    k_yt<PY, 1><<<grid, threads, smem, s>>>(S, d.T, tw + PY, d, Tick{});
+  }
+  return cudaGetLastError();
+}
+
+template <int NZM>
+static cudaError_t run_zt(const Dims& d, const float* Kh, cudaStream_t s) {
+  const int kb = zt_kb(d);
+  static bool attr = false;
+  if (cudaError_t e = allow_max_smem(k_zt<NZM>, attr)) return e;
+  dim3 grid(d.hx, (d.py + kb - 1) / kb);
+  k_zt<NZM><<<grid, 512, sizeof(float2) * 3ull * d.nz * kb, s>>>(d.T, Kh, d, kb);
+  return cudaGetLastError();
+}
+
+static cudaError_t dispatch_yt(const Dims& d, const float2* tw, float2* S, int dir, const Tick& tk, cudaStream_t s) {
+  switch (d.py) {
+    case 1: return run_yt<1>(d, tw, S, dir, tk, s);
+    case 4: return run_yt<4>(d, tw, S, dir, tk, s);
+    case 8: return run_yt<8>(d, tw, S, dir, tk, s);
+    case 16: return run_yt<16>(d, tw, S, dir, tk, s);
+    case 32: return run_yt<32>(d, tw, S, dir, tk, s);
+    case 64: return run_yt<64>(d, tw, S, dir, tk, s);
+    case 128: return run_yt<128>(d, tw, S, dir, tk, s);
+    case 256: return run_yt<256>(d, tw, S, dir, tk, s);
+    case 512: return run_yt<512>(d, tw, S, dir, tk, s);
+    case 1024: return run_yt<1024>(d, tw, S, dir, tk, s);
+    case 2048: return run_yt<2048>(d, tw, S, dir, tk, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+static cudaError_t dispatch_zt(const Dims& d, const float* Kh, cudaStream_t s) {
+  switch (nzm_of(d.nz)) {
+    case 1: return run_zt<1>(d, Kh, s);
+    case 2: return run_zt<2>(d, Kh, s);
+    case 4: return run_zt<4>(d, Kh, s);
+    case 8: return run_zt<8>(d, Kh, s);
+    case 16: return run_zt<16>(d, Kh, s);
+    case 32: return run_zt<32>(d, Kh, s);
+    case 64: return run_zt<64>(d, Kh, s);
+    case 128: return run_zt<128>(d, Kh, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 static cudaError_t dispatch_yz(const Dims& d, const float2* tw, float2* S, const float* Kh, int* flag, const Tick& tk,
                                cudaStream_t s) {
+  if (!mm_yz_fused(d)) {
+    if (!d.T) return cudaErrorInvalidValue;
+    if (cudaError_t e = dispatch_yt(d, tw, S, -1, tk, s)) return e;
+    if (cudaError_t e = dispatch_zt(d, Kh, s)) return e;
+    return dispatch_yt(d, tw, S, 1, Tick{}, s);
+  }
   switch (d.py) {
     case 1: return run_yz_nz<1>(d, tw, S, Kh, flag, tk, s);
     case 4: return run_yz_nz<4>(d, tw, S, Kh, flag, tk, s);
@@ -1069,7 +1227,7 @@ int launch_field_eval(const Dims& d, const Phys& ph, const StageArgs& a, const f
   if (dispatch_xfwd(d, a.m_in, tw, S, s) != cudaSuccess) return -1;
   if (dispatch_yz(d, tw, S, Kh, flag, Tick{}, s) != cudaSuccess) return -2;
   if (dispatch_x(d, ph, a, tw, S, s, a.mode != 0) != cudaSuccess) return -3;
-  return 3;
+  return 2 + mm_yz_launches(d);
 }
 
 // One stage when S already holds the x transform of a.m_in: y/z, then x inverse
@@ -1078,7 +1236,7 @@ int launch_stage(const Dims& d, const Phys& ph, const StageArgs& a, const float2
                  const float* Kh, int* flag, cudaStream_t s) {
   if (dispatch_yz(d, tw, S, Kh, flag, a.tick, s) != cudaSuccess) return -2;
   if (dispatch_x(d, ph, a, tw, S, s, 1) != cudaSuccess) return -3;
-  return 2;
+  return 1 + mm_yz_launches(d);
 }
 
 int launch_xfwd(const Dims& d, const float* m, const float2* tw, float2* S, cudaStream_t s) {
@@ -1091,7 +1249,8 @@ int launch_field_part(const Dims& d, const Phys& ph, const StageArgs& a, const f
   if (part == 0) e = dispatch_xfwd(d, a.m_in, tw, S, s);
   else if (part == 1) e = dispatch_yz(d, tw, S, Kh, flag, a.tick, s);
   else if (part == 2) e = dispatch_x(d, ph, a, tw, S, s, a.mode != 0);
-  return e == cudaSuccess ? 1 : -1;
+  if (e != cudaSuccess) return -1;
+  return part == 1 ? mm_yz_launches(d) : 1;
 }
 
 int launch_normalise(const Dims& d, float* m, int* flag, cudaStream_t s) {

@@ -75,6 +75,8 @@ extern "C" int mm_heff_noalloc(const int grid[3], double delta, double Ms, doubl
   d.N = (long long)d.nx * d.ny * d.nz;
   char why[256];
   if (!mm_supported(d, why, sizeof why)) return noalloc_fail(MM_EUNSUPPORTED, "mm_heff_noalloc: %s", why);
+  if (!mm_yz_fused(d))
+    return noalloc_fail(MM_EUNSUPPORTED, "mm_heff_noalloc: a kx column (3 x %d x %d complex) exceeds one CTA", d.nz, d.py);
   int Lmax = d.px > d.py ? d.px : d.py;
   if (Lmax < 2) Lmax = 2;
 

@@ -1,9 +1,10 @@
-"""The standard-problem-3 cubes of Table 1 (n^3, n = 8 .. 64): effective field
-and explicit-Euler steps through the C ABI vs the FP64 oracle.  The thick
-cubes (n >= 32) run the chunked z product."""
+"""The standard-problem-3 cubes of Table 1 (n^3, n = 8 .. 64, and 128^3): effective
+field and explicit-Euler steps through the C ABI vs the FP64 oracle.  The thick
+cubes (n >= 32) run the chunked z product; 128^3 runs the split y/z pass."""
 import numpy as np
 import pytest
 
+from oracle.demag import demag_at_cells
 from oracle.llg import TERM_ALL, TERM_DEMAG
 from paper_1501_07293_b300 import inputs
 
@@ -44,4 +45,19 @@ def test_sp3_cube_euler_steps(n):
     mo = to_device(film.run(to_xyz(m0), w.dt, 20, "euler"))
     assert np.abs(mg - mo).max() <= 2e-5, np.abs(mg - mo).max()
     assert np.abs(mo - m0).max() > 1e-3   # the state moves
+    s.close()
+
+
+def test_sp3_cube_128_sampled():
+    # the oracle evaluates eq. 13 at sampled cells (the whole 2M-cell source sum)
+    w = inputs.sp3_cube(128)
+    mat = w.mat
+    s = make_solver(w.grid, w.delta, Ms=mat.Ms, A=mat.A, Ku=mat.Ku, alpha=mat.alpha, gamma=mat.gamma,
+                    integrator="euler")
+    m = inputs.workload_state(w)
+    Hg = gpu_heff(s, m, TERM_DEMAG)
+    cells = [(0, 0, 0), (127, 127, 127), (64, 3, 90), (10, 100, 50), (77, 64, 0)]
+    Ho = demag_at_cells(to_xyz(m), w.mat.Ms, cells)
+    Hgc = np.array([[Hg[a, k, j, i] for a in range(3)] for (i, j, k) in cells])
+    assert np.abs(Hgc - Ho).max() <= 1e-5 * np.abs(Hg).max() * 10
     s.close()

@@ -22,7 +22,9 @@ TERMS = [TERM_EXCHANGE, TERM_ANISOTROPY, TERM_DEMAG, TERM_ZEEMAN, TERM_ALL]
 GRIDS = [(40, 10, 1), (7, 5, 3), (1, 1, 1), (2, 1, 1), (1, 9, 1), (1, 1, 7), (9, 1, 1), (16, 8, 2), (5, 130, 3), (3, 300, 1),
          (33, 17, 5), (64, 32, 4), (3, 40, 2), (100, 3, 16), (48, 48, 9),
          # thick samples: the chunked z product (17..32 and 33..64 planes), ragged chunks
-         (8, 8, 17), (5, 3, 33), (20, 9, 24), (1, 1, 40), (3, 1, 64), (24, 20, 64)]
+         (8, 8, 17), (5, 3, 33), (20, 9, 24), (1, 1, 40), (3, 1, 64), (24, 20, 64),
+         # columns beyond one CTA: the split y/z pass (y transforms and z product through a buffer)
+         (20, 200, 40), (6, 5, 100), (9, 70, 65), (1, 40, 128)]
 
 
 def _compare(grid, delta=4e-9, Ku=5e4, b_ext=(0.01, -0.02, 0.005), seed=7, self_term=True,
@@ -105,9 +107,9 @@ def test_heff_full_size_512x512x8_sampled():
     s.close()
 
 
-@pytest.mark.parametrize("grid", [(8, 8, 65), (40, 100, 64), (20, 200, 32)])
+@pytest.mark.parametrize("grid", [(8, 8, 129), (2000, 4, 4)])
 def test_unsupported_grid_is_refused_cleanly(grid):
-    # nz > 64; a kx column of 3 x 64 planes with py = 256, of 3 x 32 planes with py = 512
+    # more than 128 planes; a padded x size beyond 2048
     from paper_1501_07293_b300.solver import MM_EUNSUPPORTED, MMError
     with pytest.raises(MMError) as e:
         make_solver(grid, 4e-9)

@@ -48,11 +48,13 @@ def test_sp4_protocol_compressed_paper_mode(self_term):
     s.close()
 
 
-def test_rk4_program_stage_times_ragged_film():
+@pytest.mark.parametrize("grid,n", [((33, 17, 3), 60), ((12, 40, 70), 30)])
+def test_rk4_program_stage_times_ragged_film(grid, n):
     # ramps on all three components and a damping switch: the four RK4 stages
-    # read their own drive slots (t, t + dt/2, t + dt/2, t + dt)
+    # read their own drive slots (t, t + dt/2, t + dt/2, t + dt); the 70-plane
+    # film runs the split y/z pass, whose first kernel advances the clock
     import torch
-    grid, delta, dt, n = (33, 17, 3), 4e-9, 1e-13, 60
+    delta, dt = 4e-9, 1e-13
     segs = [(0.0, 25 * dt, (0.0, 0.05, -0.02), (0.2, -0.1, 0.05), 0.3),
             (25 * dt, 1.0, (0.2, -0.1, 0.05), (-0.1, 0.4, 0.1), 0.02)]
     m0 = inputs.random_state(grid, 31)
