@@ -105,7 +105,25 @@ __global__ void __launch_bounds__(512) k_xfwd(const float* __restrict__ m, float
 // small enough for the instruction cache.  Planes zi >= nz enter as zeros and
 // outputs zo >= nz are never stored, so the FMA block carries no bounds tests.
 // ---------------------------------------------------------------------------
+// Tensor loads of the z product: read-only global path, or plain loads when the
+// caller staged its tensor slice in shared memory (KS).
+template <bool KS>
+__device__ __forceinline__ float ldk(const float* p) {
+  if constexpr (KS) return *p;
+  else return __ldg(p);
+}
+template <bool KS>
+__device__ __forceinline__ float4 ldk4(const float* p) {
+  if constexpr (KS) return *reinterpret_cast<const float4*>(p);
+  else return __ldg(reinterpret_cast<const float4*>(p));
+}
+// Row stride of a staged tensor slice: nz + 4 for the 16-byte loads of the
+// direct product, nz + 1 for the scalar window loads of the chunked one (rows
+// then start in different banks)
 template <int NZM>
+__host__ __device__ constexpr int kst_pad() { return NZM > 16 ? 1 : 4; }
+
+template <int NZM, bool KS = false>
 __device__ __forceinline__ void zprod(int a, const float2* __restrict__ buf, int rs, int pos, int nz,
                                       const float* __restrict__ Kk, int hy, int kyf, bool mirrored,
                                       float2 (&out)[NZM]) {
@@ -118,13 +136,13 @@ __device__ __forceinline__ void zprod(int a, const float2* __restrict__ buf, int
     const bool odd_z = (p >= 4);              // xz, yz: odd in z and imaginary
     const float ys = (mirrored && odd_y) ? -1.f : 1.f;
     const float zs = odd_z ? -ys : ys;
-    const float* kp = Kk + ((long long)kyf * 6 + p) * nz;   // the nz offsets of this pair, contiguous
+    const float* kp = Kk + ((long long)kyf * 6 + p) * (KS ? nz + kst_pad<NZM>() : nz);   // the nz offsets of this pair
     float kr[NZM], kn[NZM];   // kernel at offsets +q and -q
     float2 mv[NZM];
     if (NZM % 4 == 0 && (nz & 3) == 0) {
 #pragma unroll
       for (int q4 = 0; q4 < NZM / 4; ++q4) {
-        const float4 v = (4 * q4 < nz) ? __ldg(reinterpret_cast<const float4*>(kp) + q4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 v = (4 * q4 < nz) ? ldk4<KS>(kp + 4 * q4) : make_float4(0.f, 0.f, 0.f, 0.f);
         kr[4 * q4 + 0] = ys * v.x; kn[4 * q4 + 0] = zs * v.x;
         kr[4 * q4 + 1] = ys * v.y; kn[4 * q4 + 1] = zs * v.y;
         kr[4 * q4 + 2] = ys * v.z; kn[4 * q4 + 2] = zs * v.z;
@@ -133,7 +151,7 @@ __device__ __forceinline__ void zprod(int a, const float2* __restrict__ buf, int
     } else {
 #pragma unroll
       for (int q = 0; q < NZM; ++q) {
-        const float v = (q < nz) ? __ldg(kp + q) : 0.f;
+        const float v = (q < nz) ? ldk<KS>(kp + q) : 0.f;
         kr[q] = ys * v;
         kn[q] = zs * v;
       }
@@ -159,7 +177,7 @@ __device__ __forceinline__ void zprod(int a, const float2* __restrict__ buf, int
 // groups of 10 positions with all three output components (lanes 0-29), so every
 // input of a position is read before any output of it is written with only a
 // warp-level barrier in between.
-template <int NZM, int PADS, typename KyOf>
+template <int NZM, int PADS, typename KyOf, bool KS = false>
 __device__ __forceinline__ void zprod_column(float2* buf, int rs, int len, int nz, const float* __restrict__ Kk,
                                              int hy, int py, KyOf ky_of) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -172,7 +190,7 @@ __device__ __forceinline__ void zprod_column(float2* buf, int rs, int len, int n
     if (act) {
       const int ky = ky_of(k);
       const bool mirrored = ky > py / 2;
-      zprod<NZM>(a, buf, rs, pidx<PADS>(k), nz, Kk, hy, mirrored ? py - ky : ky, mirrored, out);
+      zprod<NZM, KS>(a, buf, rs, pidx<PADS>(k), nz, Kk, hy, mirrored ? py - ky : ky, mirrored, out);
     }
     __syncwarp();
     if (act) {
@@ -190,6 +208,7 @@ __device__ __forceinline__ void zprod_column(float2* buf, int rs, int len, int n
 // 16 (c - j) + 15, a window of 31 kernel values loaded once per block.
 // Offsets with |zo - zi| >= nz only meet zero inputs or discarded outputs and
 // are read as zeros.
+template <bool KS = false>
 __device__ __forceinline__ void zprod_chunk(int a, int c, const float2* __restrict__ buf, int rs, int pos, int nz,
                                             const float* __restrict__ Kk, int kyf, bool mirrored,
                                             float2 (&out)[16]) {
@@ -203,7 +222,7 @@ __device__ __forceinline__ void zprod_chunk(int a, int c, const float2* __restri
     const bool odd_z = (p >= 4);
     const float ys = (mirrored && odd_y) ? -1.f : 1.f;
     const float zs = odd_z ? -ys : ys;
-    const float* kp = Kk + ((long long)kyf * 6 + p) * nz;
+    const float* kp = Kk + ((long long)kyf * 6 + p) * (KS ? nz + kst_pad<32>() : nz);
 #pragma unroll 1
     for (int j = 0; j < nblk; ++j) {
       const int base = 16 * (c - j) - 15;
@@ -212,7 +231,7 @@ __device__ __forceinline__ void zprod_chunk(int a, int c, const float2* __restri
       for (int t = 0; t < 31; ++t) {
         const int off = base + t;
         const int q = off < 0 ? -off : off;
-        const float v = q < nz ? __ldg(kp + q) : 0.f;
+        const float v = q < nz ? ldk<KS>(kp + q) : 0.f;
         w[t] = (off < 0 ? zs : ys) * v;
       }
       float2 mv[16];
@@ -236,7 +255,7 @@ __device__ __forceinline__ void zprod_chunk(int a, int c, const float2* __restri
 
 // Lanes take (position, output component, chunk): 3 NZM/16 lanes per position,
 // all in one warp, so the in-place write-back again needs only __syncwarp.
-template <int NZM, int PADS, typename KyOf>
+template <int NZM, int PADS, typename KyOf, bool KS = false>
 __device__ __forceinline__ void zprod_column_chunked(float2* buf, int rs, int len, int nz,
                                                      const float* __restrict__ Kk, int py, KyOf ky_of) {
   constexpr int NCH = NZM / 16;
@@ -252,7 +271,7 @@ __device__ __forceinline__ void zprod_column_chunked(float2* buf, int rs, int le
     if (act) {
       const int ky = ky_of(k);
       const bool mirrored = ky > py / 2;
-      zprod_chunk(a, c, buf, rs, pidx<PADS>(k), nz, Kk, mirrored ? py - ky : ky, mirrored, out);
+      zprod_chunk<KS>(a, c, buf, rs, pidx<PADS>(k), nz, Kk, mirrored ? py - ky : ky, mirrored, out);
     }
     __syncwarp();
     if (act) {
@@ -472,19 +491,33 @@ struct KyShift {
 
 template <int NZM>
 __global__ void __launch_bounds__(512, 1) k_zt(float2* __restrict__ T, const float* __restrict__ Kh, Dims d, int KB) {
-  extern __shared__ __align__(16) float2 zb[];   // [3 nz][KB]
+  extern __shared__ __align__(16) float2 zb[];   // [3 nz][KB], then the tensor rows of the block
   const int kx = blockIdx.x, ky0 = blockIdx.y * KB;
   const int nz = d.nz, NP = 3 * nz, py = d.py;
   const int len = py - ky0 < KB ? py - ky0 : KB;
   float2* Tk = T + (long long)kx * NP * py;
   for (int i = threadIdx.x; i < NP * len; i += blockDim.x) {
     const int p = i / len, j = i % len;
-    zb[p * KB + j] = Tk[(long long)p * py + ky0 + j];
+    cp_async8(zb + p * KB + j, Tk + (long long)p * py + ky0 + j);
   }
+  // the block's folded ky (py - ky above py/2) form one contiguous range of
+  // tensor rows [kmin, kmax]: staged in shared memory (the z product reads each
+  // value many times)
+  auto fold = [&](int ky) { return ky > py / 2 ? py - ky : ky; };
+  const int f0 = fold(ky0), f1 = fold(ky0 + len - 1);
+  const int kmin = min(f0, f1);   // at most len + 1 rows in every case
+  const int kmax = (ky0 <= py / 2 && ky0 + len - 1 >= py / 2) ? py / 2 : max(f0, f1);
+  constexpr int PAD = kst_pad<NZM>();
+  float* ks = reinterpret_cast<float*>(zb + NP * KB);
+  const float* Kg = Kh + ((long long)kx * d.hy + kmin) * 6 * nz;
+  for (int i = threadIdx.x; i < (kmax - kmin + 1) * 6 * nz; i += blockDim.x)
+    cp_async4(ks + (i / nz) * (nz + PAD) + i % nz, Kg + i);
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
-  const float* Kk = Kh + (long long)kx * d.hy * 6 * nz;
-  if constexpr (NZM > 16) zprod_column_chunked<NZM, 0>(zb, KB, len, nz, Kk, py, KyShift{ky0});
-  else zprod_column<NZM, 0>(zb, KB, len, nz, Kk, d.hy, py, KyShift{ky0});
+  const float* Kk = ks - (long long)kmin * 6 * (nz + PAD);   // indexed by the folded ky as the global table
+  if constexpr (NZM > 16) zprod_column_chunked<NZM, 0, KyShift, true>(zb, KB, len, nz, Kk, py, KyShift{ky0});
+  else zprod_column<NZM, 0, KyShift, true>(zb, KB, len, nz, Kk, d.hy, py, KyShift{ky0});
   __syncthreads();
   for (int i = threadIdx.x; i < NP * len; i += blockDim.x) {
     const int p = i / len, j = i % len;
@@ -979,13 +1012,30 @@ static cudaError_t allow_max_smem(K kernel, bool& done) {
 
 static const size_t kZtBudget = 200 * 1024;   // shared memory of one k_zt CTA (its ky block)
 
+// shared memory of a k_zt CTA with a block of kb ky: the data plus, at most,
+// the tensor rows of kb + 1 folded ky (a block that straddles py/2 folds onto
+// fewer rows)
+static size_t zt_smem(const Dims& d, int kb) {
+  return sizeof(float2) * 3ull * d.nz * kb + sizeof(float) * 6ull * (d.nz + 4) * (kb + 1);
+}
+
+// ky block of one k_zt CTA: what its shared memory holds, halved while the
+// launch would not fill two waves of the 148 SMs
 static int zt_kb(const Dims& d) {
-  int kb = (int)(kZtBudget / (sizeof(float2) * 3ull * d.nz));
+  int kb = (int)(kZtBudget / (sizeof(float2) * 3ull * d.nz + sizeof(float) * 6ull * (d.nz + 4))) - 1;
   if (kb > 128) kb = 128;
+  while (kb >= 16 && (long long)d.hx * ((d.py + kb - 1) / kb) < 2 * 148) kb /= 2;
   return kb;
 }
 
-int mm_yz_fused(const Dims& d) { return nzm_of(d.nz) <= 64 && yz_smem(d) + 64 <= kMaxSmem; }
+// The fused kernel needs the column in one CTA; thick samples with fewer kx
+// columns than SMs also take the split pass, which spreads the z product (the
+// bulk of their work, O(nz^2) per column) over ky blocks.
+int mm_yz_fused(const Dims& d) {
+  if (nzm_of(d.nz) > 64 || yz_smem(d) + 64 > kMaxSmem) return 0;
+  if (nzm_of(d.nz) >= 32 && d.hx < 148) return 0;
+  return 1;
+}
 int mm_yz_launches(const Dims& d) { return mm_yz_fused(d) ? 1 : 3; }
 
 int mm_supported(const Dims& d, char* why, int nwhy) {
@@ -1159,10 +1209,15 @@ static cudaError_t run_yt(const Dims& d, const float2* tw, float2* S, int dir, c
 template <int NZM>
 static cudaError_t run_zt(const Dims& d, const float* Kh, cudaStream_t s) {
   const int kb = zt_kb(d);
+  // one warp per task (10 positions, or one position per 3 NZM/16 lanes for
+  // NZM > 16), at most 16 warps
+  const int per_warp = NZM > 16 ? 32 / (3 * (NZM / 16)) : 10;
+  int warps = (kb + per_warp - 1) / per_warp;
+  if (warps > 16) warps = 16;
   static bool attr = false;
   if (cudaError_t e = allow_max_smem(k_zt<NZM>, attr)) return e;
   dim3 grid(d.hx, (d.py + kb - 1) / kb);
-  k_zt<NZM><<<grid, 512, sizeof(float2) * 3ull * d.nz * kb, s>>>(d.T, Kh, d, kb);
+  k_zt<NZM><<<grid, 32 * warps, zt_smem(d, kb), s>>>(d.T, Kh, d, kb);
   return cudaGetLastError();
 }
 
