@@ -249,6 +249,19 @@ int mm_adjoint(mm_ctx* ctx, int n, double dt, int ckpt_every, const float* dL_dm
  */
 int mm_get_series(mm_ctx* ctx, double* out, int max_records, int* n_records);
 
+/*
+ * Launch-shape overrides for the y/z pass (the paper has no counterpart; the
+ * knobs of paper_1501_07293_b300.tune's autotuner).  yz_route: 0 built-in
+ * choice, 1 the fused kernel (one CTA per kx column; MM_EUNSUPPORTED if a column
+ * does not fit), 2 the split pass (y transforms and z product as three kernels
+ * through a buffer, allocated here if needed; FP32 only).  zt_block: ky block of
+ * the split pass's z product, 0 built-in choice, else >= 8 (clamped to what
+ * fits a CTA).  Results are identical either way; the next mm_step re-captures
+ * its graph.  mm_get_tuning reports the route (1 or 2) and block in effect.
+ */
+int mm_set_tuning(mm_ctx* ctx, int yz_route, int zt_block);
+int mm_get_tuning(const mm_ctx* ctx, int* yz_route, int* zt_block);
+
 /* Number of kernels this context has enqueued so far (graph nodes counted per replay). */
 long long mm_launch_count(const mm_ctx* ctx);
 

@@ -605,6 +605,37 @@ extern "C" int mm_selftest_wait_timeout(mm_ctx* c, unsigned polls) {
   return MM_OK;
 }
 
+extern "C" int mm_set_tuning(mm_ctx* c, int yz_route, int zt_block) {
+  if (!c) return MM_EINVAL;
+  if (yz_route < 0 || yz_route > 2) return mm_fail(c, MM_EINVAL, "mm_set_tuning: yz_route %d outside 0..2", yz_route);
+  if (zt_block < 0 || (zt_block > 0 && zt_block < 8))
+    return mm_fail(c, MM_EINVAL, "mm_set_tuning: zt_block %d (0 or >= 8)", zt_block);
+  if (yz_route == 1 && !mm_yz_fits(c->d))
+    return mm_fail(c, MM_EUNSUPPORTED, "mm_set_tuning: a kx column does not fit one CTA (no fused route)");
+  if (yz_route == 2 && c->d.prec != MM_FP32)
+    return mm_fail(c, MM_EUNSUPPORTED, "mm_set_tuning: the split precisions run the fused route only");
+  Dims d = c->d;
+  d.route = yz_route;
+  d.ztkb = zt_block;
+  if (!mm_yz_fused(d) && !c->T) {   // the split pass needs its buffer
+    if (cudaMalloc(&c->T, sizeof(float2) * (size_t)d.hx * 3 * d.nz * d.py) != cudaSuccess) {
+      cudaGetLastError();
+      return mm_fail(c, MM_ENOMEM, "mm_set_tuning: cannot allocate the split-pass buffer");
+    }
+  }
+  d.T = c->T;
+  c->d = d;
+  c->graph_valid = 0;   // the step's launches change
+  return MM_OK;
+}
+
+extern "C" int mm_get_tuning(const mm_ctx* c, int* yz_route, int* zt_block) {
+  if (!c || !yz_route || !zt_block) return MM_EINVAL;
+  *yz_route = mm_yz_fused(c->d) ? 1 : 2;
+  *zt_block = mm_zt_kb(c->d);
+  return MM_OK;
+}
+
 extern "C" int mm_get_series(mm_ctx* c, double* out, int max_records, int* n_records) {
   if (!c) return MM_EINVAL;
   if (!n_records || (max_records > 0 && !out)) return mm_fail(c, MM_EINVAL, "mm_get_series: NULL output");

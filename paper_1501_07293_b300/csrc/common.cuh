@@ -34,6 +34,8 @@ struct Dims {
   const float* Kt;             // [hx][PZ/2 + 1][6][hy] tensor transformed along z as well
   const unsigned char* Bdft;   // the two DFT matrices, hi and lo, canonical shared-memory layout
   float2* T;                   // split y/z pass (columns beyond one CTA): [hx][3 nz][py] (else null)
+  int route;                   // y/z pass: 0 built-in choice, 1 fused kernel, 2 split pass (mm_set_tuning)
+  int ztkb;                    // split pass: ky block of the z product (0: built-in choice)
 };
 
 // Per-cell physics constants, float32, precomputed in double on the host.
@@ -187,6 +189,12 @@ int mm_nzm(int nz);
 int mm_yz_fused(const Dims& d);
 // field.cu: kernels one y/z pass launches (1 fused, 3 split)
 int mm_yz_launches(const Dims& d);
+// field.cu: 1 if a kx column fits one CTA (the fused kernel can run at all)
+int mm_yz_fits(const Dims& d);
+// field.cu: the largest ky block of the split pass's z product that fits a CTA
+int mm_zt_kb_max(const Dims& d);
+// field.cu: the ky block the split pass uses
+int mm_zt_kb(const Dims& d);
 
 // Same set-up into caller-provided buffers (Kc: 6 nz px py double2 scratch); returns kernels launched or < 0.
 int mm_setup_kernel_into(const Dims& d, int self_term, double2* Kc, float* Kh, cudaStream_t s);

@@ -1021,18 +1021,29 @@ static size_t zt_smem(const Dims& d, int kb) {
 
 // ky block of one k_zt CTA: what its shared memory holds, halved while the
 // launch would not fill two waves of the 148 SMs
-static int zt_kb(const Dims& d) {
+int mm_zt_kb_max(const Dims& d) {
   int kb = (int)(kZtBudget / (sizeof(float2) * 3ull * d.nz + sizeof(float) * 6ull * (d.nz + 4))) - 1;
-  if (kb > 128) kb = 128;
+  return kb > 128 ? 128 : kb;
+}
+
+static int zt_kb(const Dims& d) {
+  const int kmax = mm_zt_kb_max(d);
+  if (d.ztkb > 0) return d.ztkb < kmax ? d.ztkb : kmax;   // tuned
+  int kb = kmax;
   while (kb >= 16 && (long long)d.hx * ((d.py + kb - 1) / kb) < 2 * 148) kb /= 2;
   return kb;
 }
+int mm_zt_kb(const Dims& d) { return zt_kb(d); }
 
 // The fused kernel needs the column in one CTA; thick samples with fewer kx
 // columns than SMs also take the split pass, which spreads the z product (the
 // bulk of their work, O(nz^2) per column) over ky blocks.
+int mm_yz_fits(const Dims& d) { return nzm_of(d.nz) <= 64 && yz_smem(d) + 64 <= kMaxSmem; }
+
 int mm_yz_fused(const Dims& d) {
-  if (nzm_of(d.nz) > 64 || yz_smem(d) + 64 > kMaxSmem) return 0;
+  if (!mm_yz_fits(d)) return 0;
+  if (d.route == 1) return 1;   // tuned
+  if (d.route == 2) return d.prec ? 1 : 0;
   if (nzm_of(d.nz) >= 32 && d.hx < 148) return 0;
   return 1;
 }

@@ -64,6 +64,8 @@ _SIGNATURES = {
     "mm_step_timed": (_I, [_P, _I, _D, ctypes.POINTER(_D)]),
     "mm_adjoint": (_I, [_P, _I, _D, _I, _P, _P, _P, _P]),
     "mm_get_series": (_I, [_P, _P, _I, ctypes.POINTER(_I)]),
+    "mm_set_tuning": (_I, [_P, _I, _I]),
+    "mm_get_tuning": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "mm_launch_count": (ctypes.c_longlong, [_P]),
     "mm_sync": (_I, [_P]),
     "mm_selftest_wait_timeout": (_I, [_P, ctypes.c_uint]),
@@ -116,7 +118,7 @@ class Solver:
 
     def __init__(self, grid: Sequence[int], delta: float, Ms: float, A: float, Ku: float, alpha: float,
                  gamma: float, integrator: str = "rk4", self_term: bool = True, device=None, stream=None,
-                 precision: str = "fp32", obs_every: int = 0):
+                 precision: str = "fp32", obs_every: int = 0, tune_cache: Optional[str] = None):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
@@ -142,6 +144,10 @@ class Solver:
                 raise MMError(rc, L.mm_last_error(None).decode())
         self.ctx = ctx
         self._L = L
+        self.precision = precision
+        if tune_cache is not None:   # launch shapes an earlier autotune stored for this size
+            from .tune import apply_cached
+            apply_cached(self, tune_cache)
 
     # -- helpers --------------------------------------------------------------
     def _check(self, rc: int):
@@ -214,6 +220,16 @@ class Solver:
         n = _I(0)
         self._check(self._L.mm_get_series(self.ctx, buf.ctypes.data, int(max_records), ctypes.byref(n)))
         return buf[:n.value].copy()
+
+    def set_tuning(self, yz_route: int = 0, zt_block: int = 0):
+        """y/z launch shape: route 0 built-in / 1 fused / 2 split; z-product ky block (0 built-in)."""
+        self._check(self._L.mm_set_tuning(self.ctx, int(yz_route), int(zt_block)))
+
+    def tuning(self):
+        """(route in effect: 1 fused / 2 split, ky block of the split pass)."""
+        r, k = _I(0), _I(0)
+        self._check(self._L.mm_get_tuning(self.ctx, ctypes.byref(r), ctypes.byref(k)))
+        return r.value, k.value
 
     def time(self) -> float:
         """The context clock (s); synchronises."""
