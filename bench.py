@@ -432,6 +432,7 @@ def bench_sp3(args, steps=500, warmup=20):
     import torch
     from paper_1501_07293_b300 import inputs
     from paper_1501_07293_b300.solver import Solver
+    from paper_1501_07293_b300.tune import autotune
     stream = torch.cuda.current_stream()
     rows = []
     for n in (8, 16, 32, 64, 128):
@@ -439,6 +440,7 @@ def bench_sp3(args, steps=500, warmup=20):
         mat = w.mat
         s = Solver(w.grid, w.delta, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma, integrator="euler")
         s.set_m(torch.from_numpy(inputs.workload_state(w)).cuda())
+        tuned = autotune(s, w.dt)   # the y/z launch shape for this size (fused or split, ky block)
         s.step(warmup, w.dt)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -448,6 +450,7 @@ def bench_sp3(args, steps=500, warmup=20):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         rows.append({"n": n, "ms_per_step": ms, "cell_steps_per_s": n ** 3 / (ms * 1e-3),
+                     "yz_route": "fused" if tuned["yz_route"] == 1 else f"split, ky block {s.tuning()[1]}",
                      "paper_gtx650ti_single_ms": TABLE1_GPU_SINGLE_MS.get(n)})
         s.close()
     return {"workload": "muMAG standard problem 3 cube n^3, Euler, FP32, one field evaluation per step",
