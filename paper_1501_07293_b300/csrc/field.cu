@@ -764,7 +764,7 @@ __device__ __forceinline__ float& rowf(float2* row, int x) {
   return (x & 1) ? e.y : e.x;
 }
 
-template <int HALF>
+template <int HALF, int TYV = XTile<HALF>::v>
 __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float2* __restrict__ S,
                                        const float2* __restrict__ twP, const Dims& d, int TY, int fwd, int z,
                                        int y0) {
@@ -795,7 +795,7 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
     constexpr int P = 2 * HALF;
     constexpr int PADS = 4;
     constexpr int RS = HALF + (HALF + 1) / 16 + 2;
-    constexpr int TY = XTile<HALF>::v;   // rows per tile (the launcher uses the same value)
+    constexpr int TY = TYV;   // rows per tile (the launcher uses the same value)
     constexpr int XV = 2;                 // cells per thread of the vector update
     extern __shared__ float2 sm[];
     float2* tws = sm;
@@ -941,14 +941,14 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
 // program's drive slot (a.drive, device memory) instead of the kernel parameters
 // (a separate instantiation, so the constant-field kernel keeps them as
 // constant-bank operands).
-template <int HALF, bool DRIVE>
+template <int HALF, bool DRIVE, int TYV>
 __global__ void __launch_bounds__(512) k_x(StageArgs a, Phys ph, float2* __restrict__ S,
                                            const float2* __restrict__ twP, Dims d, int TY, int fwd) {
   if constexpr (DRIVE) {
     ph.bx = a.drive[0]; ph.by = a.drive[1]; ph.bz = a.drive[2];
     ph.g1 = a.drive[3]; ph.g2 = a.drive[4];
   }
-  body_x<HALF>(a, ph, S, twP, d, TY, fwd, blockIdx.y, blockIdx.x * TY);
+  body_x<HALF, TYV>(a, ph, S, twP, d, TY, fwd, blockIdx.y, blockIdx.x * TY);
 }
 
 // ---------------------------------------------------------------------------
@@ -991,8 +991,8 @@ static size_t yz_smem(const Dims& d) {
   if (d.prec) b += mm_nzm(d.nz) == 8 ? zs::Dft<8>::bytes : zs::Dft<16>::bytes;
   return b;
 }
-static size_t x_smem(int half) {
-  return half == 0 ? 0 : sizeof(float2) * ((size_t)2 * half + 3ull * x_tile(half) * x_rs(half));
+static size_t x_smem(int half, int ty = 0) {
+  return half == 0 ? 0 : sizeof(float2) * ((size_t)2 * half + 3ull * (ty ? ty : x_tile(half)) * x_rs(half));
 }
 
 static const size_t kMaxSmem = 227 * 1024;
@@ -1096,11 +1096,11 @@ static cudaError_t run_xfwd(const Dims& d, const float* m, const float2* tw, flo
 }
 
 // --- x inverse + update (+ forward of the new state) -------------------------
-template <int HALF>
-static cudaError_t run_x(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
-                         cudaStream_t s, int fwd) {
+template <int HALF, int TYV>
+static cudaError_t run_x_ty(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
+                            cudaStream_t s, int fwd) {
   const int P = HALF == 0 ? 1 : 2 * HALF;
-  const int TY = HALF == 0 ? 32 : x_tile(HALF);
+  const int TY = HALF == 0 ? 32 : TYV;
   const int T = HALF == 0 ? 1 : TeamOf<(HALF > 0 ? HALF : 1)>::v;
   int threads = HALF == 0 ? 32 : ((3 * TY + 1) / 2) * T;
   threads = (threads + 31) / 32 * 32;
@@ -1108,14 +1108,31 @@ static cudaError_t run_x(const Dims& d, const Phys& ph, const StageArgs& a, cons
   if (threads > 512) threads = 512;
   static bool attr = false, attr_d = false;
   dim3 grid((d.ny + TY - 1) / TY, d.nz, 1);
+  const size_t sm = x_smem(HALF, HALF == 0 ? 0 : TY);
   if (a.drive) {
-    if (cudaError_t e = allow_max_smem(k_x<HALF, true>, attr_d)) return e;
-    k_x<HALF, true><<<grid, threads, x_smem(HALF), s>>>(a, ph, S, tw + P, d, TY, fwd);
+    if (cudaError_t e = allow_max_smem(k_x<HALF, true, TYV>, attr_d)) return e;
+    k_x<HALF, true, TYV><<<grid, threads, sm, s>>>(a, ph, S, tw + P, d, TY, fwd);
   } else {
-    if (cudaError_t e = allow_max_smem(k_x<HALF, false>, attr)) return e;
-    k_x<HALF, false><<<grid, threads, x_smem(HALF), s>>>(a, ph, S, tw + P, d, TY, fwd);
+    if (cudaError_t e = allow_max_smem(k_x<HALF, false, TYV>, attr)) return e;
+    k_x<HALF, false, TYV><<<grid, threads, sm, s>>>(a, ph, S, tw + P, d, TY, fwd);
   }
   return cudaGetLastError();
+}
+
+// Rows per tile: the default, or 2 / 1 while fewer tiles than SMs would leave
+// most of them idle (small films such as the paper's 166 x 42 x 1 run: 6 tiles
+// of 8 rows, 42 of 1)
+template <int HALF>
+static cudaError_t run_x(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
+                         cudaStream_t s, int fwd) {
+  constexpr int TD = XTile<HALF>::v;
+  if constexpr (HALF >= 4 && HALF <= 256) {
+    if ((long long)((d.ny + TD - 1) / TD) * d.nz < 148) {
+      if ((long long)((d.ny + 1) / 2) * d.nz >= 148) return run_x_ty<HALF, 2>(d, ph, a, tw, S, s, fwd);
+      return run_x_ty<HALF, 1>(d, ph, a, tw, S, s, fwd);
+    }
+  }
+  return run_x_ty<HALF, TD>(d, ph, a, tw, S, s, fwd);
 }
 
 #define MM_HALF_SWITCH(px, CALL)              \
