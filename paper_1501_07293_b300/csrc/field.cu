@@ -16,9 +16,13 @@
 //                           the RK4 / Euler update and renormalisation; when
 //                           stepping it also transforms the new state forward
 //                           along x into S, so that a stage is k_yz + k_x.
+//  k_yt, k_zt               the y/z pass split in three launches, for kx
+//                           columns beyond one CTA or thick samples with few
+//                           columns (the y transforms and the z product meet
+//                           in a global buffer).
+// The split-precision z product (tensor cores) lives in zsplit.cuh.
 #include <stdio.h>
 
-#include <cooperative_groups.h>
 #include <type_traits>
 
 #include "common.cuh"
@@ -27,7 +31,6 @@
 #include "program.cuh"
 #include "zsplit.cuh"
 
-namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------------------
 // k_xfwd: CTA = (tile of TY rows along y, plane z, component c)
@@ -285,10 +288,6 @@ __device__ __forceinline__ void zprod_column_chunked(float2* buf, int rs, int le
 
 struct KyIdentity {
   __device__ int operator()(int k) const { return k; }
-};
-struct KySubband {
-  int q;
-  __device__ int operator()(int k) const { return 2 * k + q; }
 };
 
 // ---------------------------------------------------------------------------
@@ -750,7 +749,7 @@ __device__ __forceinline__ void cell_updateV(const StageArgs& a, const Phys& ph,
 // Inverse x transform of the field (complex-to-real, first nx points), the
 // per-cell update, and -- when `fwd` is set -- the forward x transform of the
 // state just written, stored back into the same tile of S for the next field
-// evaluation (so a stage needs only k_yz2 + k_x).
+// evaluation (so a stage needs only k_yz + k_x).
 // ---------------------------------------------------------------------------
 // Rows per tile of the x kernels.
 template <int HALF>
