@@ -43,6 +43,42 @@ Phys mm_make_phys(const mm_ctx* c) {
   return ph;
 }
 
+// The tensor map of S for the x kernel's tiled loads: a 4-D float view
+// {2 ny, nz, 3, hx} of S[kx][c][z][y] (float2), tile {2 TY, 1, 3, 129}.  Needs
+// ny even (16-byte row strides) and 8 <= px <= 512 (two tiles of 129 kx, 8
+// rows per tile); otherwise, or if the driver has no encoder, the kernel keeps
+// its per-thread copies.  The encoder is taken from the driver through the
+// runtime, so the library does not link the driver library itself.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static void make_xmap(mm_ctx* c) {
+  const Dims& d = c->d;
+  if (d.ny % 2 != 0 || d.px < 8 || d.px > 512) return;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return;
+  }
+  CUtensorMap* m = (CUtensorMap*)aligned_alloc(64, sizeof(CUtensorMap));
+  if (!m) return;
+  const cuuint64_t dims[4] = {2ull * d.ny, (cuuint64_t)d.nz, 3ull, (cuuint64_t)d.hx};
+  const cuuint64_t strides[3] = {8ull * d.ny, 8ull * d.ny * d.nz, 24ull * d.ny * d.nz};
+  const cuuint32_t box[4] = {16u, 1u, 3u, 129u};
+  const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  const CUresult r = ((EncodeTiledFn)fn)(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)c->S, dims, strides, box, estr,
+                                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    free(m);
+    return;
+  }
+  c->xmap = m;
+}
+
 static void drop_graphs(mm_ctx* c) {
   for (int i = 0; i < 2; ++i)
     if (c->graph[i]) {
@@ -68,6 +104,7 @@ static void free_ctx(mm_ctx* c) {
   cudaFree(c->hmap); cudaFree(c->kumap); cudaFree(c->S); cudaFree(c->Kh); cudaFree(c->tw);
   cudaFree(c->red); cudaFree(c->red_out); cudaFree(c->dflag); cudaFree(c->prog);
   cudaFree(c->Kt); cudaFree(c->Bdft); cudaFree(c->series); cudaFree(c->T);
+  free(c->xmap);
   mm_adjoint_free(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->ev) cudaEventDestroy(c->ev);
@@ -166,6 +203,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double M
     rc = mm_fail(nullptr, MM_ECUDA, "memset failed");
     goto fail;
   }
+  make_xmap(c);
   if (c->series && cudaMemsetAsync(c->series, 0, sizeof(double) * 6 * (size_t)c->series_cap, c->stream) != cudaSuccess) {
     rc = mm_fail(nullptr, MM_ECUDA, "memset failed");
     goto fail;
@@ -285,6 +323,7 @@ static StageArgs base_args(mm_ctx* c) {
   a.hmap = c->hmap;
   a.kumap = c->kumap;
   a.drive = drive_slot(c, 4);
+  a.xmap = c->xmap;
   return a;
 }
 

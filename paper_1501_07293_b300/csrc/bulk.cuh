@@ -86,6 +86,19 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Tiled 4-D tensor copy global -> shared (TMA), completing on an mbarrier with
+// the tile's bytes.  tmap: the address of a __grid_constant__ CUtensorMap
+// parameter; c0 is the innermost coordinate (its byte offset must be a
+// multiple of 16).
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
+          smem_u32(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Hint: bring the 128-byte line at p into L2 (no register result, no fault on
 // an address inside an allocation).
 __device__ __forceinline__ void prefetch_l2(const void* p) {

@@ -13,6 +13,7 @@
 //                                             length L sits at offset L
 //   hx = px/2 + 1, hy = py/2 + 1 (1 when the padded size is 1).
 #pragma once
+#include <cuda.h>   // CUtensorMap (a type only; the encoder comes through the runtime)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -89,6 +90,8 @@ struct StageArgs {
   const float* kumap;  // per-cell Ku (J/m^3) or null
   const float* drive;  // if set: bx, by, bz, g1, g2 of this evaluation (device), replacing Phys's
   Tick tick;           // launch_stage: passed to its y/z launch
+  const CUtensorMap* xmap;   // host: tensor map of S for the x kernel's tile loads (null: per-thread copies)
+  int* flag;           // device error flags ([1] <- a bounded wait gave up); set by the launchers
   int mode;
   int stage;           // RK4 stage 0..3
   unsigned mask;       // mode 0: MM_TERM_* terms to write
@@ -115,6 +118,7 @@ struct mm_ctx {
   ProgState* prog;           // clock, field program and the drive values the stages read
   double* series;            // obs_every > 0: ring of records (t, step, <mx>, <my>, <mz>, max|dm/dt|)
   int series_cap;            // records in the ring
+  CUtensorMap* xmap;         // tensor map of S (64-byte aligned host memory) or null
   float* Kt;                 // split precision: tensor transformed along z ([hx][PZ/2+1][6][hy])
   float2* T;                 // split y/z pass buffer (columns beyond one CTA's shared memory)
   unsigned char* Bdft;       // split precision: DFT operands (device)

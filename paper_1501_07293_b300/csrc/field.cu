@@ -22,6 +22,7 @@
 //                           in a global buffer).
 // The split-precision z product (tensor cores) lives in zsplit.cuh.
 #include <stdio.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -763,10 +764,13 @@ __device__ __forceinline__ float& rowf(float2* row, int x) {
   return (x & 1) ? e.y : e.x;
 }
 
-template <int HALF, int TYV = XTile<HALF>::v>
+// TMA: the S tile arrives as two tiled tensor copies (kx 0..128 and 129..257)
+// into a staging area [kx][c][TY] (xmap: the tensor map of S), instead of
+// per-thread copies; the C2R pre-processing then reads the staging area.
+template <int HALF, int TYV = XTile<HALF>::v, bool TMA = false>
 __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float2* __restrict__ S,
                                        const float2* __restrict__ twP, const Dims& d, int TY, int fwd, int z,
-                                       int y0) {
+                                       int y0, const CUtensorMap* xmap = nullptr) {
   if constexpr (HALF == 0) {
     float kmax = 0.f;
     for (int r = threadIdx.x; r < TY; r += blockDim.x) {
@@ -800,27 +804,13 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
     float2* tws = sm;
     float2* rows = sm + P;   // [3][TY] rows, element k at pidx(k), k <= HALF
     const int total = (HALF + 1) * 3 * TY;
-    // the tile of S arrives by asynchronous copies (all in flight at once)
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-      const int r = i % TY, rest = i / TY;
-      const int c = rest % 3, k = rest / 3;
-      const int y = y0 + r;
-      float2* dst = rows + (c * TY + r) * RS + pidx<PADS>(k);
-      if (y < d.ny) cp_async8(dst, S + (((long long)k * 3 + c) * d.nz + z) * d.ny + y);
-      else *dst = make_float2(0.f, 0.f);
-    }
-    cp_async_commit();
-    for (int i = threadIdx.x; i < P; i += blockDim.x) tws[i] = twP[i];
-    cp_async_wait_all();
-    __syncthreads();
-    // Z[k] = (X[k] + conj X[HALF-k]) + i W_P^{-k} (X[k] - conj X[HALF-k]), k < HALF
     const int NR = 3 * TY;
     const int npair = HALF / 2 + 1;
-    for (int i = threadIdx.x; i < NR * npair; i += blockDim.x) {
-      const int rr = i / npair, k = i % npair;
+    // Z[k] = (X[k] + conj X[HALF-k]) + i W_P^{-k} (X[k] - conj X[HALF-k]), k < HALF,
+    // for the pair (k, HALF - k) of row rr
+    auto pre_pair = [&](int rr, int k, float2 Xa, float2 Xb) {
       float2* row = rows + rr * RS;
       const int k2 = HALF - k;
-      const float2 Xa = row[pidx<PADS>(k)], Xb = row[pidx<PADS>(k2)];
       const float2 w = tws[k];
       const float2 wm = make_float2(w.x, -w.y);
       const float2 Za = cadd(cadd(Xa, cconj(Xb)), cmuli(cmul(csub(Xa, cconj(Xb)), wm)));
@@ -831,6 +821,60 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
         const float2 Zb = cadd(cadd(Xb, cconj(Xa)), cmuli(cmul(csub(Xb, cconj(Xa)), wm2)));
         row[pidx<PADS>(k)] = Za;
         row[pidx<PADS>(k2)] = Zb;
+      }
+    };
+    if constexpr (TMA) {
+      static_assert(HALF >= 4 && HALF <= 256, "two boxes of 129 kx");
+      constexpr int XB = 129;   // kx per tensor copy (two cover hx <= 257)
+      constexpr uint32_t box_bytes = XB * 3 * TY * sizeof(float2);
+      // two staging boxes [kx][c][TY] after the rows, each on a 128-byte boundary
+      float2* rend = rows + 3 * TY * RS;
+      const uint32_t s0 = (smem_u32(rend) + 127u) & ~127u;
+      const uint32_t s1 = (s0 + box_bytes + 127u) & ~127u;
+      float2* stg0 = rend + (s0 - smem_u32(rend)) / sizeof(float2);
+      float2* stg1 = stg0 + (s1 - s0) / sizeof(float2);
+      __shared__ __align__(8) uint64_t xbar;
+      if (threadIdx.x == 0) {
+        mbar_init(&xbar, 1);
+        mbar_fence_init();
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&xbar, 2 * box_bytes);
+        tma_load_4d(stg0, xmap, 2 * y0, z, 0, 0, &xbar);    // x: float index of y0 (a multiple of 16)
+        tma_load_4d(stg1, xmap, 2 * y0, z, 0, XB, &xbar);
+      }
+      for (int i = threadIdx.x; i < P; i += blockDim.x) tws[i] = twP[i];
+      const bool ok = mbar_wait_bounded(&xbar, 0);
+      if (!__syncthreads_and(ok)) {   // uniform exit; copies in flight get one more bounded wait
+        if (threadIdx.x == 0 && a.flag) atomicOr(a.flag + 1, 1);
+        mbar_wait_bounded(&xbar, 0);
+        return;
+      }
+      // rows fastest: the staging reads are contiguous across lanes
+      for (int i = threadIdx.x; i < NR * npair; i += blockDim.x) {
+        const int r = i % TY, c = (i / TY) % 3, k = i / (3 * TY), kb = HALF - k;
+        const float2 Xa = k < XB ? stg0[(k * 3 + c) * TY + r] : stg1[((k - XB) * 3 + c) * TY + r];
+        const float2 Xb = kb < XB ? stg0[(kb * 3 + c) * TY + r] : stg1[((kb - XB) * 3 + c) * TY + r];
+        pre_pair(c * TY + r, k, Xa, Xb);
+      }
+    } else {
+      // the tile of S arrives by asynchronous copies (all in flight at once)
+      for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int r = i % TY, rest = i / TY;
+        const int c = rest % 3, k = rest / 3;
+        const int y = y0 + r;
+        float2* dst = rows + (c * TY + r) * RS + pidx<PADS>(k);
+        if (y < d.ny) cp_async8(dst, S + (((long long)k * 3 + c) * d.nz + z) * d.ny + y);
+        else *dst = make_float2(0.f, 0.f);
+      }
+      cp_async_commit();
+      for (int i = threadIdx.x; i < P; i += blockDim.x) tws[i] = twP[i];
+      cp_async_wait_all();
+      __syncthreads();
+      for (int i = threadIdx.x; i < NR * npair; i += blockDim.x) {
+        const int rr = i / npair, k = i % npair;
+        pre_pair(rr, k, rows[rr * RS + pidx<PADS>(k)], rows[rr * RS + pidx<PADS>(HALF - k)]);
       }
     }
     __syncthreads();
@@ -940,14 +984,17 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
 // program's drive slot (a.drive, device memory) instead of the kernel parameters
 // (a separate instantiation, so the constant-field kernel keeps them as
 // constant-bank operands).
-template <int HALF, bool DRIVE, int TYV>
-__global__ void __launch_bounds__(512) k_x(StageArgs a, Phys ph, float2* __restrict__ S,
-                                           const float2* __restrict__ twP, Dims d, int TY, int fwd) {
+template <int HALF, bool DRIVE, int TYV, bool TMA>
+// At most 384 threads (3 TY / 2 teams of 32 lanes for 8-row tiles); two CTAs
+// per SM up to px = 512 (the long rows beyond need the registers)
+__global__ void __launch_bounds__(384, HALF >= 512 ? 1 : 2) k_x(StageArgs a, Phys ph, float2* __restrict__ S,
+                                           const float2* __restrict__ twP, Dims d, int TY, int fwd,
+                                           const __grid_constant__ CUtensorMap xmap) {
   if constexpr (DRIVE) {
     ph.bx = a.drive[0]; ph.by = a.drive[1]; ph.bz = a.drive[2];
     ph.g1 = a.drive[3]; ph.g2 = a.drive[4];
   }
-  body_x<HALF, TYV>(a, ph, S, twP, d, TY, fwd, blockIdx.y, blockIdx.x * TY);
+  body_x<HALF, TYV, TMA>(a, ph, S, twP, d, TY, fwd, blockIdx.y, blockIdx.x * TY, &xmap);
 }
 
 // ---------------------------------------------------------------------------
@@ -990,8 +1037,10 @@ static size_t yz_smem(const Dims& d) {
   if (d.prec) b += mm_nzm(d.nz) == 8 ? zs::Dft<8>::bytes : zs::Dft<16>::bytes;
   return b;
 }
-static size_t x_smem(int half, int ty = 0) {
-  return half == 0 ? 0 : sizeof(float2) * ((size_t)2 * half + 3ull * (ty ? ty : x_tile(half)) * x_rs(half));
+static size_t x_smem(int half, int ty = 0, bool tma = false) {
+  if (half == 0) return 0;
+  const int t = ty ? ty : x_tile(half);
+  return sizeof(float2) * ((size_t)2 * half + 3ull * t * x_rs(half) + (tma ? 2ull * 129 * 3 * t + 32 : 0));
 }
 
 static const size_t kMaxSmem = 227 * 1024;
@@ -1095,7 +1144,7 @@ static cudaError_t run_xfwd(const Dims& d, const float* m, const float2* tw, flo
 }
 
 // --- x inverse + update (+ forward of the new state) -------------------------
-template <int HALF, int TYV>
+template <int HALF, int TYV, bool TMA>
 static cudaError_t run_x_ty(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
                             cudaStream_t s, int fwd) {
   const int P = HALF == 0 ? 1 : 2 * HALF;
@@ -1107,13 +1156,16 @@ static cudaError_t run_x_ty(const Dims& d, const Phys& ph, const StageArgs& a, c
   if (threads > 512) threads = 512;
   static bool attr = false, attr_d = false;
   dim3 grid((d.ny + TY - 1) / TY, d.nz, 1);
-  const size_t sm = x_smem(HALF, HALF == 0 ? 0 : TY);
+  const size_t sm = x_smem(HALF, HALF == 0 ? 0 : TY, TMA);
+  alignas(64) CUtensorMap map;
+  if (TMA) map = *a.xmap;
+  else memset(&map, 0, sizeof map);
   if (a.drive) {
-    if (cudaError_t e = allow_max_smem(k_x<HALF, true, TYV>, attr_d)) return e;
-    k_x<HALF, true, TYV><<<grid, threads, sm, s>>>(a, ph, S, tw + P, d, TY, fwd);
+    if (cudaError_t e = allow_max_smem(k_x<HALF, true, TYV, TMA>, attr_d)) return e;
+    k_x<HALF, true, TYV, TMA><<<grid, threads, sm, s>>>(a, ph, S, tw + P, d, TY, fwd, map);
   } else {
-    if (cudaError_t e = allow_max_smem(k_x<HALF, false, TYV>, attr)) return e;
-    k_x<HALF, false, TYV><<<grid, threads, sm, s>>>(a, ph, S, tw + P, d, TY, fwd);
+    if (cudaError_t e = allow_max_smem(k_x<HALF, false, TYV, TMA>, attr)) return e;
+    k_x<HALF, false, TYV, TMA><<<grid, threads, sm, s>>>(a, ph, S, tw + P, d, TY, fwd, map);
   }
   return cudaGetLastError();
 }
@@ -1127,11 +1179,12 @@ static cudaError_t run_x(const Dims& d, const Phys& ph, const StageArgs& a, cons
   constexpr int TD = XTile<HALF>::v;
   if constexpr (HALF >= 4 && HALF <= 256) {
     if ((long long)((d.ny + TD - 1) / TD) * d.nz < 148) {
-      if ((long long)((d.ny + 1) / 2) * d.nz >= 148) return run_x_ty<HALF, 2>(d, ph, a, tw, S, s, fwd);
-      return run_x_ty<HALF, 1>(d, ph, a, tw, S, s, fwd);
+      if ((long long)((d.ny + 1) / 2) * d.nz >= 148) return run_x_ty<HALF, 2, false>(d, ph, a, tw, S, s, fwd);
+      return run_x_ty<HALF, 1, false>(d, ph, a, tw, S, s, fwd);
     }
+    if (a.xmap) return run_x_ty<HALF, TD, true>(d, ph, a, tw, S, s, fwd);
   }
-  return run_x_ty<HALF, TD>(d, ph, a, tw, S, s, fwd);
+  return run_x_ty<HALF, TD, false>(d, ph, a, tw, S, s, fwd);
 }
 
 #define MM_HALF_SWITCH(px, CALL)              \
@@ -1306,9 +1359,11 @@ static cudaError_t dispatch_yz(const Dims& d, const float2* tw, float2* S, const
 // Field evaluation from scratch (mode 0): x forward of a.m_in, y/z, x inverse.
 int launch_field_eval(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
                       const float* Kh, int* flag, cudaStream_t s) {
+  StageArgs ax = a;
+  ax.flag = flag;
   if (dispatch_xfwd(d, a.m_in, tw, S, s) != cudaSuccess) return -1;
   if (dispatch_yz(d, tw, S, Kh, flag, Tick{}, s) != cudaSuccess) return -2;
-  if (dispatch_x(d, ph, a, tw, S, s, a.mode != 0) != cudaSuccess) return -3;
+  if (dispatch_x(d, ph, ax, tw, S, s, a.mode != 0) != cudaSuccess) return -3;
   return 2 + mm_yz_launches(d);
 }
 
@@ -1316,8 +1371,10 @@ int launch_field_eval(const Dims& d, const Phys& ph, const StageArgs& a, const f
 // + update + x forward of the new state (S then holds the transform of a.m_out).
 int launch_stage(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
                  const float* Kh, int* flag, cudaStream_t s) {
+  StageArgs ax = a;
+  ax.flag = flag;
   if (dispatch_yz(d, tw, S, Kh, flag, a.tick, s) != cudaSuccess) return -2;
-  if (dispatch_x(d, ph, a, tw, S, s, 1) != cudaSuccess) return -3;
+  if (dispatch_x(d, ph, ax, tw, S, s, 1) != cudaSuccess) return -3;
   return 1 + mm_yz_launches(d);
 }
 
@@ -1330,7 +1387,11 @@ int launch_field_part(const Dims& d, const Phys& ph, const StageArgs& a, const f
   cudaError_t e = cudaErrorInvalidValue;
   if (part == 0) e = dispatch_xfwd(d, a.m_in, tw, S, s);
   else if (part == 1) e = dispatch_yz(d, tw, S, Kh, flag, a.tick, s);
-  else if (part == 2) e = dispatch_x(d, ph, a, tw, S, s, a.mode != 0);
+  else if (part == 2) {
+    StageArgs ax = a;
+    ax.flag = flag;
+    e = dispatch_x(d, ph, ax, tw, S, s, a.mode != 0);
+  }
   if (e != cudaSuccess) return -1;
   return part == 1 ? mm_yz_launches(d) : 1;
 }
