@@ -99,6 +99,14 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0,
       : "memory");
 }
 
+// Tiled 4-D tensor copy shared -> global (TMA store, bulk async-group; elements
+// outside the tensor are not written).  Coordinates as tma_load_4d (none negative).
+__device__ __forceinline__ void tma_store_4d(const void* tmap, const void* src, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(tmap),
+               "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+               : "memory");
+}
+
 // Hint: bring the 128-byte line at p into L2 (no register result, no fault on
 // an address inside an allocation).
 __device__ __forceinline__ void prefetch_l2(const void* p) {

@@ -947,7 +947,50 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
       team_fft_io<HALF, T, -1, 2, PADS, PADS, PADS>(rows + rr * RS, t, mask, tws, nin, HALF);
     }
     __syncthreads();
-    // X[k] = 1/2 (Z[k] + conj Z[-k]) - i/2 W_P^k (Z[k] - conj Z[-k]), in place by pairs (k, HALF-k)
+    // X[k] = 1/2 (Z[k] + conj Z[-k]) - i/2 W_P^k (Z[k] - conj Z[-k]), by pairs (k, HALF-k)
+    if constexpr (TMA) {
+      // into the staging boxes (rows fastest), then two tensor stores of the tile
+      constexpr int XB = 129;
+      constexpr uint32_t box_bytes = XB * 3 * TY * sizeof(float2);
+      float2* rend = rows + 3 * TY * RS;
+      const uint32_t s0 = (smem_u32(rend) + 127u) & ~127u;
+      const uint32_t s1 = (s0 + box_bytes + 127u) & ~127u;
+      float2* stg0 = rend + (s0 - smem_u32(rend)) / sizeof(float2);
+      float2* stg1 = stg0 + (s1 - s0) / sizeof(float2);
+      auto put = [&](int k, int c, int r, float2 v) {
+        if (k < XB) stg0[(k * 3 + c) * TY + r] = v;
+        else stg1[((k - XB) * 3 + c) * TY + r] = v;
+      };
+      for (int i = threadIdx.x; i < NR * npair; i += blockDim.x) {
+        const int r = i % TY, c = (i / TY) % 3, k = i / (3 * TY);
+        const float2* row = rows + (c * TY + r) * RS;
+        const int k2 = HALF - k;
+        if (k == 0) {
+          const float2 z0 = row[pidx<PADS>(0)];
+          put(0, c, r, make_float2(z0.x + z0.y, 0.f));
+          put(HALF, c, r, make_float2(z0.x - z0.y, 0.f));
+        } else if (k == k2) {
+          put(k, c, r, cconj(row[pidx<PADS>(k)]));
+        } else {
+          const float2 zk = row[pidx<PADS>(k)], zc = row[pidx<PADS>(k2)];
+          const float2 w = tws[k];
+          const float2 d1 = csub(zk, cconj(zc));
+          put(k, c, r, cscale(cadd(cadd(zk, cconj(zc)), cmul(make_float2(d1.y, -d1.x), w)), 0.5f));
+          const float2 w2 = make_float2(-w.x, w.y);            // W_P^{HALF-k} = -conj W_P^k
+          const float2 d2 = csub(zc, cconj(zk));
+          put(k2, c, r, cscale(cadd(cadd(zc, cconj(zk)), cmul(make_float2(d2.y, -d2.x), w2)), 0.5f));
+        }
+      }
+      fence_proxy_async_smem();   // the tensor stores read the staging area (async proxy)
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tma_store_4d(xmap, stg0, 2 * y0, z, 0, 0);
+        tma_store_4d(xmap, stg1, 2 * y0, z, 0, XB);
+        bulk_commit();
+        bulk_wait_read_all();   // the staging area stays valid until the stores have read it
+      }
+      return;
+    }
     for (int i = threadIdx.x; i < NR * npair; i += blockDim.x) {
       const int rr = i / npair, k = i % npair;
       float2* row = rows + rr * RS;
