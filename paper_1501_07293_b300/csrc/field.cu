@@ -294,15 +294,20 @@ struct KyIdentity {
 // ---------------------------------------------------------------------------
 // k_yz: CTA = one kx column, all 3 components and nz planes in shared memory.
 //  1. the column's 3 nz rows of ny values arrive by bulk copies (TMA engine)
-//     into dense rows of a padded buffer (row stride RS);
+//     into dense rows of a padded buffer (row stride RS), issued in up to
+//     YZ_GROUPS groups of rows with one mbarrier each;
 //  2. forward y transform of every row: the first pass reads the dense row and
 //     takes positions >= ny as zeros (zero padding), the later passes use the
-//     padded layout (no shared-memory bank conflicts);
+//     padded layout (no shared-memory bank conflicts).  A team waits only for
+//     its row's group, so the first transforms overlap the later copies;
 //  3. the product of eq. 14 along z (zprod_column), in place;
 //  4. inverse y transform; the last pass writes only the first ny outputs, dense;
-//  5. bulk copies back to S.
+//  5. each team bulk-copies its row back to S as soon as the row is done, so the
+//     stores overlap the remaining inverse transforms.
 // A failed bounded wait sets flag[1] and abandons the column.
 // ---------------------------------------------------------------------------
+static constexpr int YZ_GROUPS = 8;   // copy groups (mbarriers) of the y/z column
+
 template <int PY>
 struct YzLayout {
   static constexpr int PADS = PY >= 32 ? 4 : 0;
@@ -322,20 +327,27 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   extern __shared__ __align__(16) float2 sm[];
   float2* tws = sm;        // exp(-2 pi i m / PY), m < PY
   float2* buf = sm + PY;   // [3 nz][RS]
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar[YZ_GROUPS];
   const int nz = d.nz, ny = d.ny;
   const int NP = 3 * nz;
   float2* Sk = S + (long long)kx * NP * ny;
   const bool bulk = (ny % 2) == 0;   // rows of ny float2 are then 16-byte multiples
+  // rows p of group g: g * rpg <= p < min(NP, (g + 1) * rpg)
+  const int rpg = (NP + YZ_GROUPS - 1) / YZ_GROUPS;
+  const int ngrp = (NP + rpg - 1) / rpg;
   if (bulk) {
     if (threadIdx.x == 0) {
-      mbar_init(&bar, 1);
+      for (int g = 0; g < ngrp; ++g) mbar_init(&bar[g], 1);
       mbar_fence_init();
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      mbar_arrive_expect_tx(&bar, (uint32_t)(NP * ny * sizeof(float2)));
-      for (int p = 0; p < NP; ++p) bulk_g2s(buf + p * RS, Sk + (long long)p * ny, ny * sizeof(float2), &bar);
+      for (int g = 0; g < ngrp; ++g) {
+        const int p1 = min(NP, (g + 1) * rpg);
+        mbar_arrive_expect_tx(&bar[g], (uint32_t)((p1 - g * rpg) * ny * sizeof(float2)));
+        for (int p = g * rpg; p < p1; ++p)
+          bulk_g2s(buf + p * RS, Sk + (long long)p * ny, ny * sizeof(float2), &bar[g]);
+      }
     }
   } else {
     for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) buf[(i / ny) * RS + i % ny] = Sk[i];
@@ -365,32 +377,37 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
     const int nlines = (bytes + 127) >> 7;
     for (int i = threadIdx.x; i < nlines; i += blockDim.x) prefetch_l2(kc + ((long long)i << 7));
   }
+  __syncthreads();   // the twiddles (and the per-thread copies of the rows)
   // first y/z pass of a step: the last warp of CTA 0 advances the field
   // program's clock and writes the drive slots while the copies land (the x
   // kernels that follow read them; nothing in this kernel does)
   if (tk.p && kx == 0 && threadIdx.x >= blockDim.x - 32) prog_tick(tk);
-  const bool arrived = !bulk || mbar_wait_bounded(&bar, 0);
+  const int lane = threadIdx.x & 31;
+  const int team = threadIdx.x / T, t = threadIdx.x % T, nteams = blockDim.x / T;
+  const unsigned mask = team_mask<T>(lane);
+  bool arrived = true;
+  if (PY > 1) {
+    for (int p = team; p < NP; p += nteams) {
+      if (bulk) arrived = mbar_wait_bounded(&bar[p / rpg], 0) && arrived;
+      team_fft_io<PY, T, -1, 1, 0, PADS, PADS>(buf + p * RS, t, mask, tws, ny, PY);
+    }
+  } else if (bulk) {
+    for (int g = 0; g < ngrp; ++g) arrived = mbar_wait_bounded(&bar[g], 0) && arrived;
+  }
   if constexpr (PREC != 0) {
     fence_proxy_async_smem();   // the DFT operands are read by the tensor cores (async proxy)
     zs::fence_before();
   }
   if (!__syncthreads_and(arrived)) {   // uniform: every thread leaves, tensor memory is freed
     if (threadIdx.x == 0) atomicOr(flag + 1, 1);
-    if (bulk) mbar_wait_bounded(&bar, 0);   // copies in flight get one more bounded chance
+    if (bulk)   // copies in flight get one more bounded chance
+      for (int g = 0; g < ngrp; ++g) mbar_wait_bounded(&bar[g], 0);
     if constexpr (PREC != 0) {
       if ((threadIdx.x >> 5) == 0) zs::tmem_dealloc(tbase, 512);
     }
     return;
   }
   if constexpr (PREC != 0) zs::fence_after();
-  const int lane = threadIdx.x & 31;
-  const int team = threadIdx.x / T, t = threadIdx.x % T, nteams = blockDim.x / T;
-  const unsigned mask = team_mask<T>(lane);
-  if (PY > 1) {
-    for (int p = team; p < NP; p += nteams)
-      team_fft_io<PY, T, -1, 1, 0, PADS, PADS>(buf + p * RS, t, mask, tws, ny, PY);
-    __syncthreads();
-  }
   // Product of eq. 14 along z (see zprod).
   if constexpr (PREC != 0) {
     static_assert(NZM == 8 || NZM == 16, "split z product: 8 or 16 planes");
@@ -412,19 +429,25 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   else
     zprod_column<NZM, 0>(buf, RS, PY, nz, Kh + (long long)kx * 6 * nz * d.hy, d.hy, PY, KyIdentity());
   __syncthreads();
-  if (PY > 1) {
-    for (int p = team; p < NP; p += nteams)
-      team_fft_io<PY, T, 1, 1, PADS, PADS, 0>(buf + p * RS, t, mask, tws, PY, ny);
-    __syncthreads();
-  }
   if (bulk) {
-    if (threadIdx.x == 0) {
+    // each team stores its own rows: every lane orders its writes of the row
+    // before the bulk engine's reads, then the team's first lane issues the copy
+    for (int p = team; p < NP; p += nteams) {
+      if (PY > 1) team_fft_io<PY, T, 1, 1, PADS, PADS, 0>(buf + p * RS, t, mask, tws, PY, ny);
       fence_proxy_async_smem();
-      for (int p = 0; p < NP; ++p) bulk_s2g(Sk + (long long)p * ny, buf + p * RS, ny * sizeof(float2));
-      bulk_commit();
-      bulk_wait_read_all();
+      __syncwarp(mask);
+      if (t == 0) {
+        bulk_s2g(Sk + (long long)p * ny, buf + p * RS, ny * sizeof(float2));
+        bulk_commit();
+      }
     }
+    if (t == 0) bulk_wait_read_all();   // the rows stay valid until read
   } else {
+    if (PY > 1) {
+      for (int p = team; p < NP; p += nteams)
+        team_fft_io<PY, T, 1, 1, PADS, PADS, 0>(buf + p * RS, t, mask, tws, PY, ny);
+      __syncthreads();
+    }
     for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) Sk[i] = buf[(i / ny) * RS + i % ny];
   }
 }
