@@ -112,3 +112,12 @@ __device__ __forceinline__ void tma_store_4d(const void* tmap, const void* src, 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
+
+// Programmatic dependent launch (sm_90 and later).  grid_dep_wait: wait until
+// the grids this one depends on have completed and their writes are visible
+// (returns at once when the kernel was launched without such a dependency).
+// grid_dep_launch: let the next kernel in the stream, if it was launched with
+// programmatic serialization, start its blocks; it still orders every access to
+// this grid's results after its own grid_dep_wait.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }

@@ -25,6 +25,7 @@
 #include <string.h>
 
 #include <type_traits>
+#include <utility>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -335,26 +336,15 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   // rows p of group g: g * rpg <= p < min(NP, (g + 1) * rpg)
   const int rpg = (NP + YZ_GROUPS - 1) / YZ_GROUPS;
   const int ngrp = (NP + rpg - 1) / rpg;
-  if (bulk) {
-    if (threadIdx.x == 0) {
-      for (int g = 0; g < ngrp; ++g) mbar_init(&bar[g], 1);
-      mbar_fence_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int g = 0; g < ngrp; ++g) {
-        const int p1 = min(NP, (g + 1) * rpg);
-        mbar_arrive_expect_tx(&bar[g], (uint32_t)((p1 - g * rpg) * ny * sizeof(float2)));
-        for (int p = g * rpg; p < p1; ++p)
-          bulk_g2s(buf + p * RS, Sk + (long long)p * ny, ny * sizeof(float2), &bar[g]);
-      }
-    }
-  } else {
-    for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) buf[(i / ny) * RS + i % ny] = Sk[i];
+  // Prologue on constant data only (barriers, twiddles, the tensor's L2
+  // prefetch, the split path's operands): with programmatic serialization it
+  // overlaps the end of the kernel before, which wrote S.
+  if (bulk && threadIdx.x == 0) {
+    for (int g = 0; g < ngrp; ++g) mbar_init(&bar[g], 1);
+    mbar_fence_init();
   }
   for (int i = threadIdx.x; i < PY; i += blockDim.x) tws[i] = twY[i];
-  // split precision: the DFT operands, the MMA barrier and the tensor memory,
-  // set up while the column's copies are in flight
+  // split precision: the DFT operands, the MMA barrier and the tensor memory
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tbase;
   unsigned char* Bsm = reinterpret_cast<unsigned char*>(buf + 3 * nz * RS);
@@ -377,7 +367,22 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
     const int nlines = (bytes + 127) >> 7;
     for (int i = threadIdx.x; i < nlines; i += blockDim.x) prefetch_l2(kc + ((long long)i << 7));
   }
-  __syncthreads();   // the twiddles (and the per-thread copies of the rows)
+  grid_dep_wait();     // S and the program state: written by the kernels before
+  grid_dep_launch();
+  __syncthreads();     // barriers initialised, twiddles in place
+  if (bulk) {
+    if (threadIdx.x == 0) {
+      for (int g = 0; g < ngrp; ++g) {
+        const int p1 = min(NP, (g + 1) * rpg);
+        mbar_arrive_expect_tx(&bar[g], (uint32_t)((p1 - g * rpg) * ny * sizeof(float2)));
+        for (int p = g * rpg; p < p1; ++p)
+          bulk_g2s(buf + p * RS, Sk + (long long)p * ny, ny * sizeof(float2), &bar[g]);
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) buf[(i / ny) * RS + i % ny] = Sk[i];
+    __syncthreads();
+  }
   // first y/z pass of a step: the last warp of CTA 0 advances the field
   // program's clock and writes the drive slots while the copies land (the x
   // kernels that follow read them; nothing in this kernel does)
@@ -1056,6 +1061,8 @@ template <int HALF, bool DRIVE, int TYV, bool TMA>
 __global__ void __launch_bounds__(384, HALF >= 512 ? 1 : 2) k_x(StageArgs a, Phys ph, float2* __restrict__ S,
                                            const float2* __restrict__ twP, Dims d, int TY, int fwd,
                                            const __grid_constant__ CUtensorMap xmap) {
+  grid_dep_wait();     // S, the stage states and the drive slots: written by the kernels before
+  grid_dep_launch();
   if constexpr (DRIVE) {
     ph.bx = a.drive[0]; ph.by = a.drive[1]; ph.bz = a.drive[2];
     ph.g1 = a.drive[3]; ph.g2 = a.drive[4];
@@ -1192,6 +1199,25 @@ int mm_supported(const Dims& d, char* why, int nwhy) {
   return 1;
 }
 
+// Launch with programmatic stream serialization: the kernel's blocks may start
+// while the kernel before it in the stream drains, and wait (grid_dep_wait)
+// before they touch anything that kernel writes.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 // --- x forward (prologue: S <- transform of a state) ------------------------
 template <int HALF>
 static cudaError_t run_xfwd(const Dims& d, const float* m, const float2* tw, float2* S, cudaStream_t s) {
@@ -1226,14 +1252,13 @@ static cudaError_t run_x_ty(const Dims& d, const Phys& ph, const StageArgs& a, c
   alignas(64) CUtensorMap map;
   if (TMA) map = *a.xmap;
   else memset(&map, 0, sizeof map);
+  const float2* twP = tw + P;
   if (a.drive) {
     if (cudaError_t e = allow_max_smem(k_x<HALF, true, TYV, TMA>, attr_d)) return e;
-    k_x<HALF, true, TYV, TMA><<<grid, threads, sm, s>>>(a, ph, S, tw + P, d, TY, fwd, map);
-  } else {
-    if (cudaError_t e = allow_max_smem(k_x<HALF, false, TYV, TMA>, attr)) return e;
-    k_x<HALF, false, TYV, TMA><<<grid, threads, sm, s>>>(a, ph, S, tw + P, d, TY, fwd, map);
+    return launch_pdl(k_x<HALF, true, TYV, TMA>, grid, dim3(threads), sm, s, a, ph, S, twP, d, TY, fwd, map);
   }
-  return cudaGetLastError();
+  if (cudaError_t e = allow_max_smem(k_x<HALF, false, TYV, TMA>, attr)) return e;
+  return launch_pdl(k_x<HALF, false, TYV, TMA>, grid, dim3(threads), sm, s, a, ph, S, twP, d, TY, fwd, map);
 }
 
 // Rows per tile: the default, or 2 / 1 while fewer tiles than SMs would leave
@@ -1291,19 +1316,18 @@ static cudaError_t run_yz_t(const Dims& d, const float2* tw, float2* S, const fl
       static bool attr1 = false, attr2 = false;
       if (d.prec == MM_SPLIT_BF16) {
         if (cudaError_t e = allow_max_smem(k_yz<PY, NZM, MM_SPLIT_BF16>, attr1)) return e;
-        k_yz<PY, NZM, MM_SPLIT_BF16><<<d.hx, 512, yz_smem(d), s>>>(S, Kh, tw + PY, d, flag, tk);
-      } else {
-        if (cudaError_t e = allow_max_smem(k_yz<PY, NZM, MM_SPLIT_FP16>, attr2)) return e;
-        k_yz<PY, NZM, MM_SPLIT_FP16><<<d.hx, 512, yz_smem(d), s>>>(S, Kh, tw + PY, d, flag, tk);
+        return launch_pdl(k_yz<PY, NZM, MM_SPLIT_BF16>, dim3(d.hx), dim3(512), yz_smem(d), s, S, Kh, tw + PY, d,
+                          flag, tk);
       }
-      return cudaGetLastError();
+      if (cudaError_t e = allow_max_smem(k_yz<PY, NZM, MM_SPLIT_FP16>, attr2)) return e;
+      return launch_pdl(k_yz<PY, NZM, MM_SPLIT_FP16>, dim3(d.hx), dim3(512), yz_smem(d), s, S, Kh, tw + PY, d,
+                        flag, tk);
     }
   }
   if (d.prec) return cudaErrorInvalidValue;
   static bool attr = false;
   if (cudaError_t e = allow_max_smem(k_yz<PY, NZM, 0>, attr)) return e;
-  k_yz<PY, NZM, 0><<<d.hx, 512, yz_smem(d), s>>>(S, Kh, tw + PY, d, flag, tk);
-  return cudaGetLastError();
+  return launch_pdl(k_yz<PY, NZM, 0>, dim3(d.hx), dim3(512), yz_smem(d), s, S, Kh, tw + PY, d, flag, tk);
 }
 
 #define MM_NZ_SWITCH(nz, CALL)          \
