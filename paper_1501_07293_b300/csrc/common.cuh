@@ -37,6 +37,7 @@ struct Dims {
   float2* T;                   // split y/z pass (columns beyond one CTA): [hx][3 nz][py] (else null)
   int route;                   // y/z pass: 0 built-in choice, 1 fused kernel, 2 split pass (mm_set_tuning)
   int ztkb;                    // split pass: ky block of the z product (0: built-in choice)
+  int pdl;                     // stage kernels launched with programmatic serialization (large grids)
 };
 
 // Per-cell physics constants, float32, precomputed in double on the host.

@@ -295,19 +295,21 @@ struct KyIdentity {
 // ---------------------------------------------------------------------------
 // k_yz: CTA = one kx column, all 3 components and nz planes in shared memory.
 //  1. the column's 3 nz rows of ny values arrive by bulk copies (TMA engine)
-//     into dense rows of a padded buffer (row stride RS), issued in up to
-//     YZ_GROUPS groups of rows with one mbarrier each;
+//     into dense rows of a padded buffer (row stride RS);
 //  2. forward y transform of every row: the first pass reads the dense row and
 //     takes positions >= ny as zeros (zero padding), the later passes use the
-//     padded layout (no shared-memory bank conflicts).  A team waits only for
-//     its row's group, so the first transforms overlap the later copies;
+//     padded layout (no shared-memory bank conflicts);
 //  3. the product of eq. 14 along z (zprod_column), in place;
 //  4. inverse y transform; the last pass writes only the first ny outputs, dense;
-//  5. each team bulk-copies its row back to S as soon as the row is done, so the
-//     stores overlap the remaining inverse transforms.
+//  5. bulk copies back to S.
+// On large grids (d.pdl: the first wave of CTAs starts together, right when the
+// kernel before completes) the copies of step 1 go in up to YZ_GROUPS groups of
+// rows with one mbarrier each, a team waiting only for its row's group, and in
+// step 5 each team stores its rows as soon as they are done.  Small films keep
+// one barrier and one storing thread (cheaper when launch-bound).
 // A failed bounded wait sets flag[1] and abandons the column.
 // ---------------------------------------------------------------------------
-static constexpr int YZ_GROUPS = 8;   // copy groups (mbarriers) of the y/z column
+static constexpr int YZ_GROUPS = 8;   // copy groups (mbarriers) of a y/z column on large grids
 
 template <int PY>
 struct YzLayout {
@@ -328,20 +330,41 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   extern __shared__ __align__(16) float2 sm[];
   float2* tws = sm;        // exp(-2 pi i m / PY), m < PY
   float2* buf = sm + PY;   // [3 nz][RS]
-  __shared__ __align__(8) uint64_t bar[YZ_GROUPS];
+  // grouped copies only in the instances for tall columns (py >= 128); the
+  // short ones keep the single-barrier code alone (smaller and, for the small
+  // launch-bound films, measurably faster)
+  constexpr bool CAN_GROUP = PY >= 128;
+  __shared__ __align__(8) uint64_t bar[CAN_GROUP ? YZ_GROUPS : 1];
   const int nz = d.nz, ny = d.ny;
   const int NP = 3 * nz;
   float2* Sk = S + (long long)kx * NP * ny;
   const bool bulk = (ny % 2) == 0;   // rows of ny float2 are then 16-byte multiples
+  const bool grouped = CAN_GROUP && bulk && d.pdl;
   // rows p of group g: g * rpg <= p < min(NP, (g + 1) * rpg)
-  const int rpg = (NP + YZ_GROUPS - 1) / YZ_GROUPS;
+  const int rpg = grouped ? (NP + YZ_GROUPS - 1) / YZ_GROUPS : NP;
   const int ngrp = (NP + rpg - 1) / rpg;
-  // Prologue on constant data only (barriers, twiddles, the tensor's L2
-  // prefetch, the split path's operands): with programmatic serialization it
-  // overlaps the end of the kernel before, which wrote S.
+  auto issue_copies = [&] {
+    for (int g = 0; g < ngrp; ++g) {
+      const int p1 = min(NP, (g + 1) * rpg);
+      mbar_arrive_expect_tx(&bar[g], (uint32_t)((p1 - g * rpg) * ny * sizeof(float2)));
+      for (int p = g * rpg; p < p1; ++p)
+        bulk_g2s(buf + p * RS, Sk + (long long)p * ny, ny * sizeof(float2), &bar[g]);
+    }
+  };
   if (bulk && threadIdx.x == 0) {
     for (int g = 0; g < ngrp; ++g) mbar_init(&bar[g], 1);
     mbar_fence_init();
+  }
+  // Without programmatic serialization (small grids) the kernel starts after
+  // the one before has completed: the copies go out first and land during the
+  // prologue.  With it, the prologue below touches constant data only
+  // (twiddles, the tensor's L2 prefetch, the split path's operands) and
+  // overlaps the end of the kernel before, which wrote S; the copies follow
+  // the dependency wait.
+  const bool early = bulk && !d.pdl;
+  if (early) {
+    __syncthreads();   // the barriers are initialised before anyone polls them
+    if (threadIdx.x == 0) issue_copies();
   }
   for (int i = threadIdx.x; i < PY; i += blockDim.x) tws[i] = twY[i];
   // split precision: the DFT operands, the MMA barrier and the tensor memory
@@ -369,19 +392,13 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   }
   grid_dep_wait();     // S and the program state: written by the kernels before
   grid_dep_launch();
-  __syncthreads();     // barriers initialised, twiddles in place
-  if (bulk) {
-    if (threadIdx.x == 0) {
-      for (int g = 0; g < ngrp; ++g) {
-        const int p1 = min(NP, (g + 1) * rpg);
-        mbar_arrive_expect_tx(&bar[g], (uint32_t)((p1 - g * rpg) * ny * sizeof(float2)));
-        for (int p = g * rpg; p < p1; ++p)
-          bulk_g2s(buf + p * RS, Sk + (long long)p * ny, ny * sizeof(float2), &bar[g]);
-      }
+  if (!early) {
+    __syncthreads();   // the barriers are initialised before anyone polls them
+    if (bulk) {
+      if (threadIdx.x == 0) issue_copies();
+    } else {
+      for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) buf[(i / ny) * RS + i % ny] = Sk[i];
     }
-  } else {
-    for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) buf[(i / ny) * RS + i % ny] = Sk[i];
-    __syncthreads();
   }
   // first y/z pass of a step: the last warp of CTA 0 advances the field
   // program's clock and writes the drive slots while the copies land (the x
@@ -391,13 +408,13 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   const int team = threadIdx.x / T, t = threadIdx.x % T, nteams = blockDim.x / T;
   const unsigned mask = team_mask<T>(lane);
   bool arrived = true;
-  if (PY > 1) {
+  if (grouped) {   // transforms start on the rows that have landed
     for (int p = team; p < NP; p += nteams) {
-      if (bulk) arrived = mbar_wait_bounded(&bar[p / rpg], 0) && arrived;
-      team_fft_io<PY, T, -1, 1, 0, PADS, PADS>(buf + p * RS, t, mask, tws, ny, PY);
+      arrived = mbar_wait_bounded(&bar[p / rpg], 0) && arrived;
+      if (PY > 1) team_fft_io<PY, T, -1, 1, 0, PADS, PADS>(buf + p * RS, t, mask, tws, ny, PY);
     }
   } else if (bulk) {
-    for (int g = 0; g < ngrp; ++g) arrived = mbar_wait_bounded(&bar[g], 0) && arrived;
+    arrived = mbar_wait_bounded(&bar[0], 0);
   }
   if constexpr (PREC != 0) {
     fence_proxy_async_smem();   // the DFT operands are read by the tensor cores (async proxy)
@@ -413,6 +430,11 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
     return;
   }
   if constexpr (PREC != 0) zs::fence_after();
+  if (PY > 1 && !grouped) {
+    for (int p = team; p < NP; p += nteams)
+      team_fft_io<PY, T, -1, 1, 0, PADS, PADS>(buf + p * RS, t, mask, tws, ny, PY);
+    __syncthreads();
+  }
   // Product of eq. 14 along z (see zprod).
   if constexpr (PREC != 0) {
     static_assert(NZM == 8 || NZM == 16, "split z product: 8 or 16 planes");
@@ -434,7 +456,7 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   else
     zprod_column<NZM, 0>(buf, RS, PY, nz, Kh + (long long)kx * 6 * nz * d.hy, d.hy, PY, KyIdentity());
   __syncthreads();
-  if (bulk) {
+  if (grouped) {
     // each team stores its own rows: every lane orders its writes of the row
     // before the bulk engine's reads, then the team's first lane issues the copy
     for (int p = team; p < NP; p += nteams) {
@@ -447,12 +469,21 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
       }
     }
     if (t == 0) bulk_wait_read_all();   // the rows stay valid until read
-  } else {
-    if (PY > 1) {
-      for (int p = team; p < NP; p += nteams)
-        team_fft_io<PY, T, 1, 1, PADS, PADS, 0>(buf + p * RS, t, mask, tws, PY, ny);
-      __syncthreads();
+    return;
+  }
+  if (PY > 1) {
+    for (int p = team; p < NP; p += nteams)
+      team_fft_io<PY, T, 1, 1, PADS, PADS, 0>(buf + p * RS, t, mask, tws, PY, ny);
+    __syncthreads();
+  }
+  if (bulk) {
+    if (threadIdx.x == 0) {
+      fence_proxy_async_smem();
+      for (int p = 0; p < NP; ++p) bulk_s2g(Sk + (long long)p * ny, buf + p * RS, ny * sizeof(float2));
+      bulk_commit();
+      bulk_wait_read_all();
     }
+  } else {
     for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) Sk[i] = buf[(i / ny) * RS + i % ny];
   }
 }
@@ -489,6 +520,8 @@ __global__ void __launch_bounds__(256) k_yt(float2* __restrict__ S, float2* __re
   float2* Sk = S + (long long)kx * NP * ny;
   float2* Tk = T + (long long)kx * NP * PY;
   for (int i = threadIdx.x; i < PY; i += blockDim.x) tws[i] = twY[i];
+  grid_dep_wait();     // S or T: written by the kernel before
+  grid_dep_launch();
   const int nin = DIR < 0 ? ny : PY;
   for (int i = threadIdx.x; i < nrows * nin; i += blockDim.x) {
     const int r = i / nin, e = i % nin;
@@ -524,13 +557,10 @@ __global__ void __launch_bounds__(512, 1) k_zt(float2* __restrict__ T, const flo
   const int nz = d.nz, NP = 3 * nz, py = d.py;
   const int len = py - ky0 < KB ? py - ky0 : KB;
   float2* Tk = T + (long long)kx * NP * py;
-  for (int i = threadIdx.x; i < NP * len; i += blockDim.x) {
-    const int p = i / len, j = i % len;
-    cp_async8(zb + p * KB + j, Tk + (long long)p * py + ky0 + j);
-  }
   // the block's folded ky (py - ky above py/2) form one contiguous range of
   // tensor rows [kmin, kmax]: staged in shared memory (the z product reads each
-  // value many times)
+  // value many times).  The tensor is constant, so its copies start before the
+  // dependency wait; T is written by the kernel before.
   auto fold = [&](int ky) { return ky > py / 2 ? py - ky : ky; };
   const int f0 = fold(ky0), f1 = fold(ky0 + len - 1);
   const int kmin = min(f0, f1);   // at most len + 1 rows in every case
@@ -540,6 +570,12 @@ __global__ void __launch_bounds__(512, 1) k_zt(float2* __restrict__ T, const flo
   const float* Kg = Kh + ((long long)kx * d.hy + kmin) * 6 * nz;
   for (int i = threadIdx.x; i < (kmax - kmin + 1) * 6 * nz; i += blockDim.x)
     cp_async4(ks + (i / nz) * (nz + PAD) + i % nz, Kg + i);
+  grid_dep_wait();
+  grid_dep_launch();
+  for (int i = threadIdx.x; i < NP * len; i += blockDim.x) {
+    const int p = i / len, j = i % len;
+    cp_async8(zb + p * KB + j, Tk + (long long)p * py + ky0 + j);
+  }
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
@@ -1199,12 +1235,12 @@ int mm_supported(const Dims& d, char* why, int nwhy) {
   return 1;
 }
 
-// Launch with programmatic stream serialization: the kernel's blocks may start
-// while the kernel before it in the stream drains, and wait (grid_dep_wait)
-// before they touch anything that kernel writes.
+// Launch with programmatic stream serialization (when d.pdl): the kernel's
+// blocks may start while the kernel before it in the stream drains, and wait
+// (grid_dep_wait) before they touch anything that kernel writes.
 template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                              Args&&... args) {
+static cudaError_t launch_pdl(const Dims& d, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t s, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -1214,7 +1250,7 @@ static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = d.pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
@@ -1255,10 +1291,10 @@ static cudaError_t run_x_ty(const Dims& d, const Phys& ph, const StageArgs& a, c
   const float2* twP = tw + P;
   if (a.drive) {
     if (cudaError_t e = allow_max_smem(k_x<HALF, true, TYV, TMA>, attr_d)) return e;
-    return launch_pdl(k_x<HALF, true, TYV, TMA>, grid, dim3(threads), sm, s, a, ph, S, twP, d, TY, fwd, map);
+    return launch_pdl(d, k_x<HALF, true, TYV, TMA>, grid, dim3(threads), sm, s, a, ph, S, twP, d, TY, fwd, map);
   }
   if (cudaError_t e = allow_max_smem(k_x<HALF, false, TYV, TMA>, attr)) return e;
-  return launch_pdl(k_x<HALF, false, TYV, TMA>, grid, dim3(threads), sm, s, a, ph, S, twP, d, TY, fwd, map);
+  return launch_pdl(d, k_x<HALF, false, TYV, TMA>, grid, dim3(threads), sm, s, a, ph, S, twP, d, TY, fwd, map);
 }
 
 // Rows per tile: the default, or 2 / 1 while fewer tiles than SMs would leave
@@ -1316,18 +1352,18 @@ static cudaError_t run_yz_t(const Dims& d, const float2* tw, float2* S, const fl
       static bool attr1 = false, attr2 = false;
       if (d.prec == MM_SPLIT_BF16) {
         if (cudaError_t e = allow_max_smem(k_yz<PY, NZM, MM_SPLIT_BF16>, attr1)) return e;
-        return launch_pdl(k_yz<PY, NZM, MM_SPLIT_BF16>, dim3(d.hx), dim3(512), yz_smem(d), s, S, Kh, tw + PY, d,
+        return launch_pdl(d, k_yz<PY, NZM, MM_SPLIT_BF16>, dim3(d.hx), dim3(512), yz_smem(d), s, S, Kh, tw + PY, d,
                           flag, tk);
       }
       if (cudaError_t e = allow_max_smem(k_yz<PY, NZM, MM_SPLIT_FP16>, attr2)) return e;
-      return launch_pdl(k_yz<PY, NZM, MM_SPLIT_FP16>, dim3(d.hx), dim3(512), yz_smem(d), s, S, Kh, tw + PY, d,
+      return launch_pdl(d, k_yz<PY, NZM, MM_SPLIT_FP16>, dim3(d.hx), dim3(512), yz_smem(d), s, S, Kh, tw + PY, d,
                         flag, tk);
     }
   }
   if (d.prec) return cudaErrorInvalidValue;
   static bool attr = false;
   if (cudaError_t e = allow_max_smem(k_yz<PY, NZM, 0>, attr)) return e;
-  return launch_pdl(k_yz<PY, NZM, 0>, dim3(d.hx), dim3(512), yz_smem(d), s, S, Kh, tw + PY, d, flag, tk);
+  return launch_pdl(d, k_yz<PY, NZM, 0>, dim3(d.hx), dim3(512), yz_smem(d), s, S, Kh, tw + PY, d, flag, tk);
 }
 
 #define MM_NZ_SWITCH(nz, CALL)          \
@@ -1367,13 +1403,12 @@ static cudaError_t run_yt(const Dims& d, const float2* tw, float2* S, int dir, c
   if (dir < 0) {
     static bool attr = false;
     if (cudaError_t e = allow_max_smem(k_yt<PY, -1>, attr)) return e;
-    k_yt<PY, -1><<<grid, threads, smem, s>>>(S, d.T, tw + PY, d, tk);
+    return launch_pdl(d, k_yt<PY, -1>, grid, dim3(threads), smem, s, S, d.T, tw + PY, d, tk);
   } else {
     static bool attr = false;
     if (cudaError_t e = allow_max_smem(k_yt<PY, 1>, attr)) return e;
-    k_yt<PY, 1><<<grid, threads, smem, s>>>(S, d.T, tw + PY, d, Tick{});
+    return launch_pdl(d, k_yt<PY, 1>, grid, dim3(threads), smem, s, S, d.T, tw + PY, d, Tick{});
   }
-  return cudaGetLastError();
 }
 
 template <int NZM>
@@ -1387,8 +1422,7 @@ static cudaError_t run_zt(const Dims& d, const float* Kh, cudaStream_t s) {
   static bool attr = false;
   if (cudaError_t e = allow_max_smem(k_zt<NZM>, attr)) return e;
   dim3 grid(d.hx, (d.py + kb - 1) / kb);
-  k_zt<NZM><<<grid, 32 * warps, zt_smem(d, kb), s>>>(d.T, Kh, d, kb);
-  return cudaGetLastError();
+  return launch_pdl(d, k_zt<NZM>, grid, dim3(32 * warps), zt_smem(d, kb), s, d.T, Kh, d, kb);
 }
 
 static cudaError_t dispatch_yt(const Dims& d, const float2* tw, float2* S, int dir, const Tick& tk, cudaStream_t s) {
