@@ -1,0 +1,5 @@
+// Instances of the x pass (inverse/forward x transforms, update) for px = 2048.
+#define FIELD_INSTANTIATE
+#include "field_kernels.cuh"
+
+FK_INSTANTIATE_X(1024)
