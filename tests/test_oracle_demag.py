@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 from scipy import integrate
 
-from oracle.demag import demag_direct, demag_fft
+from oracle.demag import demag_at_cells, demag_direct, demag_fft
 from oracle.tensor import demag_tensor
 
 
@@ -87,3 +87,45 @@ def test_demag_is_linear_and_symmetric():
     Kb = demag_fft(b, 1.0, K)
     assert abs((a * Kb).sum() - (Ka * b).sum()) < 1e-13
     assert np.allclose(demag_fft(2.0 * a + b, 1.0, K), 2.0 * Ka + Kb, atol=1e-13)
+
+
+@pytest.mark.parametrize("grid", [(5, 4, 3), (7, 1, 1), (1, 6, 1), (1, 1, 5), (3, 5, 2), (1, 1, 1)])
+@pytest.mark.parametrize("self_term", [True, False])
+def test_demag_at_cells_equals_direct_sum_everywhere(grid, self_term):
+    # the sampled route of eq. 13 (used for full-size parity) is the same sum as the
+    # brute force at every cell, for both readings of the self offset
+    m = _random_unit(grid, 5)
+    K = demag_tensor(*grid, self_term=self_term)
+    Hd = demag_direct(m, 8e5, K)
+    cells = [(i, j, k) for i in range(grid[0]) for j in range(grid[1]) for k in range(grid[2])]
+    Hc = demag_at_cells(m, 8e5, cells, self_term=self_term)
+    ref = np.array([Hd[(slice(None),) + c] for c in cells])
+    assert np.abs(Hc - ref).max() <= 1e-13 * np.abs(Hd).max()
+
+
+def test_demag_at_cells_self_term_is_minus_third_of_M():
+    # a single cell: with the self offset H = -M/3 (the cube's demagnetising factors),
+    # without it H = 0
+    m = np.zeros((3, 1, 1, 1))
+    m[:, 0, 0, 0] = [0.6, -0.8, 0.0]
+    H = demag_at_cells(m, 8e5, [(0, 0, 0)])[0]
+    assert np.abs(H + 8e5 * m[:, 0, 0, 0] / 3).max() <= 1e-9
+    assert np.abs(demag_at_cells(m, 8e5, [(0, 0, 0)], self_term=False)).max() == 0.0
+
+
+@pytest.mark.parametrize("a", [0, 2])
+def test_demag_at_cells_uniform_box_matches_surface_charges(a):
+    # a uniformly magnetised 7 x 5 x 2 box, at cells away from the centre (a corner,
+    # an edge, a face): the Coulomb field of its two charged faces, by quadrature
+    # independent of eq. 10/11
+    nx, ny, nz = 7, 5, 2
+    m = np.zeros((3, nx, ny, nz))
+    m[a] = 1.0
+    Ms = 8e5
+    cells = [(0, 0, 0), (6, 4, 1), (3, 0, 1), (6, 2, 0)]
+    H = demag_at_cells(m, Ms, cells)
+    lo, hi = np.zeros(3), np.array([nx, ny, nz], float)
+    for q, cell in enumerate(cells):
+        p = np.array(cell, float) + 0.5
+        Hq = Ms * _surface_charge_field(lo, hi, p, a)
+        assert np.abs(H[q] - Hq).max() < 1e-9 * Ms
