@@ -8,7 +8,7 @@ shares no code, constant or helper with it.
 Every function follows the paper's own definitions in float64, written for a
 reader who checks it against the paper by eye: no blocking, fusion or
 reordering beyond what the definition states.  Library primitives (numpy
-arithmetic, ``numpy.fft.fftn``) serve as steps.
+arithmetic, ``scipy.fft.fftn`` on all host cores) serve as steps.
 
 Array convention of the oracle: a vector field is an array of shape
 (3, nx, ny, nz) indexed [component, i, j, k] with i along x, as in the paper's
