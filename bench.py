@@ -119,8 +119,18 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # roofline bookkeeping
 # ---------------------------------------------------------------------------
+def _padded(grid):
+    nx, ny, nz = grid
+    px = 1 if nx == 1 else 1 << (2 * nx - 2).bit_length()
+    py = 1 if ny == 1 else 1 << (2 * ny - 2).bit_length()
+    hx = 1 if px == 1 else px // 2 + 1
+    hy = 1 if py == 1 else py // 2 + 1
+    return px, py, hx, hy
+
+
 def algorithmic_bytes(grid):
-    """Compulsory HBM bytes per launch of each kernel class (FP32 RK4 stage).
+    """Compulsory HBM bytes per launch of each kernel class of this implementation
+    (FP32 RK4 stage).
 
     yz: read the x-transformed field S and the transformed tensor Kh, write S
     x:  read S, m_stage, m0; accumulator r/w (averaged over the 4 stages:
@@ -128,14 +138,32 @@ def algorithmic_bytes(grid):
     """
     nx, ny, nz = grid
     N = nx * ny * nz
-    px = 1 if nx == 1 else 1 << (2 * nx - 2).bit_length()
-    py = 1 if ny == 1 else 1 << (2 * ny - 2).bit_length()
-    hx = 1 if px == 1 else px // 2 + 1
-    hy = 1 if py == 1 else py // 2 + 1
+    px, py, hx, hy = _padded(grid)
     S = hx * 3 * nz * ny * 8
     Kh = hx * 6 * nz * hy * 4
     v = 12 * N
     return {"yz": 2 * S + Kh, "x": S + v + v + 1.5 * v + v + S}
+
+
+def method_bytes(grid):
+    """The method's algorithmic bytes per field evaluation (three passes: x forward,
+    fused y/z with the spectral product, x inverse with the LLG/RK4 update), per
+    pass, in bytes for the whole grid: the fewest a zero-padded FFT convolution
+    moves when the spectrum does not fit on chip -- one round trip of the
+    half spectrum (3 components x 8 B x hx/nx per cell) per transform direction,
+    the transformed tensor's octant (6 components x 4 B x hx hy (pz/2 + 1)) and
+    the RK4 state.  At 256 x 256 x 16: 36.1 + 73.9 + 84.1 = 194.1 B per cell and
+    evaluation, 776 B per cell and RK4 step."""
+    nx, ny, nz = grid
+    N = nx * ny * nz
+    px, py, hx, hy = _padded(grid)
+    pz = 1 if nz == 1 else 1 << (2 * nz - 2).bit_length()
+    spec = 3 * 8 * hx * ny * nz            # half spectrum after the x transform
+    tens = 6 * 4 * hx * hy * (pz // 2 + 1)  # real octant of the transformed tensor
+    a1 = 12 * N + spec                      # read m, write the spectrum
+    a2 = spec + tens + spec                 # read spectrum + tensor, write spectrum
+    a3 = spec + 12 * N + 12 * N + 24 * N + 12 * N   # spectrum, m_stage, m0, acc r/w, next stage
+    return {"a1": a1, "a2": a2, "a3": a3, "eval": a1 + a2 + a3}
 
 
 def _fft_pruned(L):
@@ -172,9 +200,10 @@ def algorithmic_flops(grid):
     return {"yz": hx * col, "x": ny * nz * 6 * rfft + 100 * nx * ny * nz}
 
 
-# FP32 peak from the unit counts and clock: 148 SMs x 128 FP32 lanes x 2 flops
-# (one fused multiply-add) x 2032 MHz maximum SM clock
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# FP32 peak derived from the unit counts and the maximum clock, used only when
+# the probe cannot run: SMs x 128 FP32 lanes x 2 flops (one FMA) x 2032 MHz
+def derived_fp32_tflops(sms):
+    return sms * 128 * 2 * 2.032e9 / 1e12
 
 
 def measured_peaks():
@@ -430,6 +459,41 @@ def bench_split(args, fp32_ms, steps=30, warmup=3):
     return out
 
 
+def bench_noalloc(args, reps=20):
+    """mm_heff_noalloc (tensor set-up + one field evaluation, no allocation) against
+    mm_heff on a context (tensor built once at creation), 128 x 128 x 4, CUDA events."""
+    import torch
+    from paper_1501_07293_b300 import inputs
+    from paper_1501_07293_b300.solver import Solver, TERM_ALL, heff_noalloc, noalloc_status
+    w = inputs.film_128x128x4()
+    mat = w.mat
+    m = torch.from_numpy(inputs.workload_state(w)).cuda()
+    s = Solver(w.grid, w.delta, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma)
+    s.set_m(m)
+    mn = s.get_m().clone()
+    H = torch.empty_like(mn)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ctx_ms = timed(lambda: s.heff(TERM_ALL, out=H))
+    na_ms = timed(lambda: heff_noalloc(w.grid, w.delta, mat.Ms, mat.A, mat.Ku, (0, 0, 0), mn, H))
+    noalloc_status()
+    s.close()
+    return {"workload": "128x128x4 effective field", "mm_heff_ms": ctx_ms, "mm_heff_noalloc_ms": na_ms,
+            "note": "mm_heff_noalloc rebuilds the FP64 tensor on every call"}
+
+
 def bench_cufft(args, ours_ms_per_stage, reps=20):
     """Timed comparison only: the demagnetising convolution of one field evaluation as
     a library pipeline -- cuFFT (through torch.fft) R2C of the three zero-padded
@@ -577,30 +641,43 @@ def b300_arm(args, w):
     names = ["yz", "x"]
     kernels = {"yz": "k_yz", "x": "k_x"}
     alg = algorithmic_bytes(w.grid)
+    meth = method_bytes(w.grid)
+    ncell = w.ncells
+    # the method's bytes per launch of each kernel class: y/z = pass a2; x = pass a3
+    # plus the spectrum write of the next stage's x transform (a1 without its read
+    # of m, which this implementation takes from registers)
+    mb = {"yz": meth["a2"], "x": meth["a3"] + meth["a1"] - 12 * ncell}
     flops = algorithmic_flops(w.grid)
     dom = max(names, key=lambda n: per_launch_ms[n])
     peak, peak_kind = measured_peaks()
+    # FP32 ceiling: measured by the library's FMA-chain probe on this device
+    from paper_1501_07293_b300.solver import fp32_probe_tflops
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32 = {"scalar_fma_tflops": fp32_probe_tflops(False, 1 << 12),
+            "packed_fma2_tflops": fp32_probe_tflops(True, 1 << 12),
+            "sms": sms, "derived_tflops": derived_fp32_tflops(sms)}
+    fp32_peak = max(fp32["scalar_fma_tflops"], fp32["packed_fma2_tflops"])
     kernel_table = {}
     for n in names:
         t = per_launch_ms[n] * 1e-3
-        # the binding ceiling: the larger of the HBM time and the FP32 time at peak
-        t_hbm, t_alu = alg[n] / (peak * 1e9), flops[n] / (FP32_PEAK_TFLOPS * 1e12)
-        kernel_table[n] = {"ms_per_launch": float(per_launch_ms[n]), "alg_bytes": float(alg[n]),
-                           "alg_flops": float(flops[n]), "GBps": float(alg[n] / t / 1e9),
+        kernel_table[n] = {"ms_per_launch": float(per_launch_ms[n]),
+                           "method_bytes": float(mb[n]), "impl_bytes": float(alg[n]),
+                           "alg_flops": float(flops[n]), "GBps": float(mb[n] / t / 1e9),
                            "TFLOPs": float(flops[n] / t / 1e12),
-                           "hbm_frac": float(alg[n] / t / 1e9 / peak),
-                           "alu_frac": float(flops[n] / t / 1e12 / FP32_PEAK_TFLOPS),
-                           "bound": "alu" if t_alu > t_hbm else "hbm"}
+                           "hbm_frac": float(mb[n] / t / 1e9 / peak),
+                           "alu_frac": float(flops[n] / t / 1e12 / fp32_peak),
+                           "hbm_floor_ms": float(mb[n] / (peak * 1e9) * 1e3),
+                           "alu_floor_ms": float(flops[n] / (fp32_peak * 1e12) * 1e3)}
     kd = kernel_table[dom]
-    if kd["bound"] == "alu":
-        roofline = {"bound": "alu", "kernel": kernels[dom], "achieved": kd["TFLOPs"], "peak": FP32_PEAK_TFLOPS,
-                    "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 flops x 2032 MHz", "unit": "TFLOP/s",
-                    "frac": kd["alu_frac"], "traffic": stored_traffic(kernels[dom]),
-                    "hbm_achieved_GBps": kd["GBps"], "hbm_peak_GBps": peak, "hbm_frac": kd["hbm_frac"]}
-    else:
-        roofline = {"bound": "hbm", "kernel": kernels[dom], "achieved": kd["GBps"], "peak": peak,
-                    "peak_kind": peak_kind, "unit": "GB/s", "frac": kd["hbm_frac"],
-                    "traffic": stored_traffic(kernels[dom])}
+    roofline = {"bound": "hbm", "kernel": kernels[dom], "achieved": kd["GBps"], "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": kd["hbm_frac"],
+                "traffic": stored_traffic(kernels[dom]),
+                "bytes_per_launch": kd["method_bytes"],
+                "bytes_model": "the method's pass a2 (y/z + product): read and write the half spectrum, "
+                               "read the tensor octant",
+                "alu": {"achieved": kd["TFLOPs"], "peak": fp32_peak, "unit": "TFLOP/s", "frac": kd["alu_frac"],
+                        "peak_kind": "measured (FMA-chain probe, the faster of scalar and packed)",
+                        "flops_per_launch": kd["alg_flops"]}}
 
     # ---- end to end through the C ABI with host buffers ----
     m_host = torch.from_numpy(m0.copy()).pin_memory()
@@ -629,6 +706,7 @@ def b300_arm(args, w):
         extra["sp3_table1"] = bench_sp3(args)
         extra["split_precision"] = bench_split(args, 1e3 * t_max / K)
         extra["cufft_comparison"] = bench_cufft(args, float(per_launch_ms["yz"] + per_launch_ms["x"]))
+        extra["noalloc"] = bench_noalloc(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -649,7 +727,9 @@ def b300_arm(args, w):
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline,
             "kernels": kernel_table,
-            "step_fraction_of_hbm_roofline": (sum(alg[n] * 4 for n in names) * K / t_max / 1e9) / peak,
+            "step_fraction_of_hbm_roofline": (4 * meth["eval"] * K / t_max / 1e9) / peak,   # per GPU
+            "step_bytes_per_cell": 4 * meth["eval"] / ncell,
+            "fp32_peak": fp32,
             "wall_s_timed_region": t_wall,
             "clocks": clk.summary(),
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,

@@ -271,9 +271,24 @@ long long mm_launch_count(const mm_ctx* ctx);
  * completes, gives up after `polls` (1 .. 2^20) polls, sets the timeout flag
  * and returns, as a kernel whose bulk copy never lands would.  The next
  * mm_sync / mm_energy / mm_observables returns MM_ETIMEOUT and clears the flag;
- * the context stays usable.
+ * the context stays usable.  With ctx NULL the flag set is that of
+ * mm_heff_noalloc's scratch on the current device (legacy default stream),
+ * reported by mm_noalloc_status.
  */
 int mm_selftest_wait_timeout(mm_ctx* ctx, unsigned polls);
+
+/*
+ * Peak-rate probe of the FP32 pipes (measurement only; the paper has no
+ * counterpart): enqueues on `stream` (a cudaStream_t; NULL = legacy default)
+ * one launch of register-resident fused multiply-add chains, 4 CTAs of 256
+ * threads per SM of the current device, `iters` (1 .. 2^24) iterations of 8
+ * independent chains per thread; packed = 1 issues the packed pair FMA
+ * (__ffma2_rn), 0 the scalar fmaf.  *flops (host) receives the floating-point
+ * operations of the launch (2 per FMA); the caller times the launch with CUDA
+ * events.  Touches no memory.  MM_EINVAL / MM_ECUDA on bad arguments / launch
+ * failure.
+ */
+int mm_fp32_probe(int packed, int iters, void* stream, double* flops);
 
 /* Block until the context's stream is idle; reports a pending device-side error. */
 int mm_sync(mm_ctx* ctx);
@@ -336,12 +351,13 @@ const char* mm_batch_last_error(const mm_batch* b);
 
 /*
  * mm_heff_noalloc -- the effective field of one state, computed without any
- * device allocation.  The paper has no counterpart: it is a service for
- * callers that cannot call cudaMalloc, for example code that runs while a
- * stream is being captured into a CUDA graph (an allocation there breaks the
- * capture), code whose device memory is handed out by another allocator that
- * already holds the GPU's free memory, or latency-sensitive code that cannot
- * afford the device-wide synchronisation cudaMalloc/cudaFree imply.
+ * device allocation.  The paper has no counterpart: it serves callers that
+ * cannot call cudaMalloc, for example a plug-in whose host application owns
+ * the GPU's memory pool and hands it out only as buffers it allocated itself,
+ * code running where a caching allocator already holds the device's free
+ * memory (a cudaMalloc there fails although the pool has room), or a
+ * latency-bound loop that cannot take the device-wide synchronisation that
+ * cudaMalloc and cudaFree imply.
  *
  * It needs no context: from grid = {nx, ny, nz}, delta, Ms, A, Ku (easy axis
  * x), b_ext = mu0 H_ext (tesla, 3 host doubles) and self_term (1 keeps the
@@ -353,6 +369,12 @@ const char* mm_batch_last_error(const mm_batch* b);
  * parameters and holding the same state.  Work is enqueued on `stream`
  * (a cudaStream_t; NULL = legacy default stream) and is asynchronous.
  *
+ * Cost: every call rebuilds the tensor (the FP64 eq. 10/11 kernel and two FP64
+ * transforms of 6 nz px py values) before its one field evaluation, while
+ * mm_heff on a context uses the tensor mm_create built once.  Measured on a
+ * B300 at 128 x 128 x 4 (CUDA events): 2.54 ms per mm_heff_noalloc call
+ * against 0.023 ms per mm_heff call.
+ *
  * All intermediate data lives in one file-scope static device array of
  * MM_NOALLOC_SCRATCH_BYTES; grids whose tensor planes (6 nz px py complex
  * doubles) plus transformed tables do not fit are refused with
@@ -360,22 +382,38 @@ const char* mm_batch_last_error(const mm_batch* b);
  * allocates, frees or calls an allocating library routine.
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call on a device uses the same array, and
- * each call writes every byte it later reads, so nothing has to be cleared
- * between calls; but two calls whose work overlaps on the GPU (different
- * streams, or different host threads) race on the array and give wrong
- * results.  Serialise them.
+ * (cudaGetSymbolAddress) with that device current, and caches it for that
+ * device's CUDA context (a new context, after cudaDeviceReset, looks it up
+ * again); make that first call before any stream capture.  Every call on a
+ * device uses the same array, and each call writes every byte of it that it
+ * later reads (the error flags excepted, see mm_noalloc_status), so nothing has
+ * to be cleared between calls; but two calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race on the array and give
+ * wrong results.  Serialise them.
  *
  * Errors: MM_EINVAL (NULL pointer, size < 1, bad parameter or mask),
  * MM_EUNSUPPORTED (too large for the array or for the kernels), MM_ECUDA
- * (launch failure); mm_noalloc_last_error() describes the last failure.
+ * (launch failure); mm_noalloc_last_error() describes the last failure of the
+ * calling thread.  Conditions found on the device while the kernels run are
+ * reported by mm_noalloc_status, not by the (asynchronous) call itself.
  */
 int mm_heff_noalloc(const int grid[3], double delta, double Ms, double A, double Ku,
                     const double b_ext[3], int self_term, const float* m_dev, float* H_dev,
                     unsigned term_mask, void* stream);
 
-/* Text of the last mm_heff_noalloc failure ("" if none). */
+/*
+ * Device-side status of the mm_heff_noalloc calls made so far on the current
+ * device: synchronises `stream` (a cudaStream_t; NULL = legacy default), reads
+ * the kernels' error flags from the scratch array and clears them.  Returns
+ * MM_ETIMEOUT if a bounded wait inside a kernel gave up (that call's H is not
+ * valid), MM_ENONFINITE if a kernel flagged a non-finite value, else MM_OK.
+ * The flags accumulate over calls until this reads them.  Allocates nothing.
+ * mm_selftest_wait_timeout(NULL, polls) sets the timeout flag on purpose, to
+ * test this path.
+ */
+int mm_noalloc_status(void* stream);
+
+/* Text of the calling thread's last mm_heff_noalloc / mm_noalloc_status failure ("" if none). */
 const char* mm_noalloc_last_error(void);
 
 #ifdef __cplusplus

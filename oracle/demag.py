@@ -52,11 +52,14 @@ def demag_direct(m, Ms, K):
     return H
 
 
-def demag_at_cells(m, Ms, cells, self_term=True):
+def demag_at_cells(m, Ms, cells, self_term=True, K=None):
     """Eq. 13 by brute force at a few target cells only (for grids too large for demag_direct).
 
-    The tensor is evaluated (eq. 10/11) at exactly the offsets l - i the sum
-    needs.  Returns an array (len(cells), 3).
+    Without K the tensor is evaluated (eq. 10/11) at exactly the offsets l - i
+    the sum needs, per target cell.  With K (the dict demag_tensor returns for
+    this grid, holding its own choice of the self offset) the offsets are
+    sliced out of it as demag_direct does, which is faster for many cells.
+    Returns an array (len(cells), 3).
     """
     _, nx, ny, nz = m.shape
     M = Ms * np.asarray(m, dtype=np.float64)
@@ -65,12 +68,19 @@ def demag_at_cells(m, Ms, cells, self_term=True):
     Nn = np.arange(nz)[None, None, :]
     out = np.zeros((len(cells), 3))
     for q, (i, j, k) in enumerate(cells):
-        K = tensor_at(L - i, Mm - j, Nn - k)
-        if not self_term:
-            for c in COMPONENTS:
-                K[c][i, j, k] = 0.0
+        if K is None:
+            Kc = tensor_at(L - i, Mm - j, Nn - k)
+            if not self_term:
+                for c in COMPONENTS:
+                    Kc[c][i, j, k] = 0.0
+        else:
+            # K(l - i, m - j, n - k) for l = 0..nx-1 sits at index (l - i) + nx - 1
+            sl = (slice(nx - 1 - i, 2 * nx - 1 - i),
+                  slice(ny - 1 - j, 2 * ny - 1 - j),
+                  slice(nz - 1 - k, 2 * nz - 1 - k))
+            Kc = {c: K[c][sl] for c in COMPONENTS}
         for a in range(3):
-            out[q, a] = sum(np.sum(M[b] * K[_PAIRS[(a, b)]]) for b in range(3))
+            out[q, a] = sum(np.sum(M[b] * Kc[_PAIRS[(a, b)]]) for b in range(3))
     return out
 
 

@@ -640,8 +640,14 @@ __global__ void k_wait_selftest(int* flag, unsigned polls) {
 }
 
 extern "C" int mm_selftest_wait_timeout(mm_ctx* c, unsigned polls) {
-  if (!c) return MM_EINVAL;
-  if (polls < 1 || polls > (1u << 20)) return mm_fail(c, MM_EINVAL, "mm_selftest_wait_timeout: polls out of range");
+  if (polls < 1 || polls > (1u << 20))
+    return c ? mm_fail(c, MM_EINVAL, "mm_selftest_wait_timeout: polls out of range") : MM_EINVAL;
+  if (!c) {   // the flags of mm_heff_noalloc's scratch on the current device
+    unsigned char* base = nullptr;
+    if (int rc = mm_noalloc_scratch(&base)) return rc;
+    k_wait_selftest<<<1, 32, 0, 0>>>((int*)base, polls);
+    return cudaGetLastError() == cudaSuccess ? MM_OK : MM_ECUDA;
+  }
   k_wait_selftest<<<1, 32, 0, c->stream>>>(c->dflag, polls);
   if (cudaGetLastError() != cudaSuccess) return mm_fail(c, MM_ECUDA, "self-test launch failed");
   c->launches++;

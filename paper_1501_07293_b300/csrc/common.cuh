@@ -144,6 +144,10 @@ struct mm_ctx {
 // adjoint.cu
 void mm_adjoint_free(mm_ctx* c);
 
+// noalloc.cu: device address of mm_heff_noalloc's static scratch on the current
+// device (looked up once per device and context); its first ints are the error flags
+int mm_noalloc_scratch(unsigned char** base);
+
 // api.cu
 Phys mm_make_phys(const mm_ctx* c);
 

@@ -2,7 +2,8 @@
 // allocation.  Every intermediate buffer (the FP64 tensor planes, the
 // transformed tensor, the x-transformed field and the twiddle tables) is carved
 // out of one file-scope static device array, so the call needs no context and
-// never calls cudaMalloc or cudaFree.  See include/mm_b300.h for the contract.
+// never calls cudaMalloc or cudaFree.  mm_noalloc_status reads back the error
+// flags its kernels set.  See include/mm_b300.h for the contract.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -15,13 +16,23 @@
 #define MM_NOALLOC_MAX_DEVICES 64
 
 // The shared scratch.  Every GPU that loads the library holds it until exit.
+// Its first 256 bytes are the kernels' error flags ([0] non-finite, [1] a
+// bounded wait gave up); static storage starts zeroed, and only
+// mm_noalloc_status clears them again.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MM_NOALLOC_SCRATCH_BYTES];
 
-// Host-side device address of g_noalloc_scratch, per device (the symbol itself
-// is only a host stand-in and must never be passed to a kernel).
-static void* g_scratch_addr[MM_NOALLOC_MAX_DEVICES];
+// Host-side device address of g_noalloc_scratch per device (the symbol itself
+// is only a host stand-in and must never be passed to a kernel), with the CUDA
+// context that was current when it was looked up: a different context on the
+// same device (after cudaDeviceReset, the module is loaded anew) looks it up
+// again.
+struct ScratchSlot {
+  void* addr;
+  void* ctx;
+};
+static ScratchSlot g_slot[MM_NOALLOC_MAX_DEVICES];
 static std::mutex g_scratch_mutex;
-static char g_noalloc_err[512] = "";
+static thread_local char g_noalloc_err[512] = "";
 
 static int noalloc_fail(int code, const char* fmt, ...) {
   va_list ap;
@@ -32,6 +43,56 @@ static int noalloc_fail(int code, const char* fmt, ...) {
 }
 
 extern "C" const char* mm_noalloc_last_error(void) { return g_noalloc_err; }
+
+// The driver's cuCtxGetCurrent, taken through the runtime (the library does not
+// link the driver library itself); null if unavailable.
+typedef int (*CtxGetCurrentFn)(void**);
+static CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)p;
+    else
+      cudaGetLastError();
+    tried = true;
+  }
+  return fn;
+}
+
+// Set-up: the device address of the scratch on the current device, looked up
+// (cudaGetSymbolAddress, with that device current) on the first call in each
+// CUDA context and cached.  Returns MM_OK or MM_ECUDA (message set).
+int mm_noalloc_scratch(unsigned char** base) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MM_NOALLOC_MAX_DEVICES) {
+    cudaGetLastError();
+    return noalloc_fail(MM_ECUDA, "mm_heff_noalloc: no usable current device");
+  }
+  CtxGetCurrentFn cur = ctx_get_current();
+  void* ctx = nullptr;
+  if (cur) cur(&ctx);
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  ScratchSlot& sl = g_slot[dev];
+  if (!sl.addr || !ctx || sl.ctx != ctx) {
+    // (the lookup also makes the device's primary context current if none was)
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return noalloc_fail(MM_ECUDA, "mm_heff_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    }
+    ctx = nullptr;
+    if (cur) cur(&ctx);
+    sl.addr = p;
+    sl.ctx = ctx;
+  }
+  *base = (unsigned char*)sl.addr;
+  return MM_OK;
+}
 
 // Twiddle tables exp(-2 pi i m / L), L = 1, 2, ..., Lmax, at offset L (double, rounded to float).
 __global__ void k_noalloc_twiddles(float2* tw, int Lmax) {
@@ -92,34 +153,15 @@ extern "C" int mm_heff_noalloc(const int grid[3], double delta, double Ms, doubl
                         "mm_heff_noalloc: grid %d x %d x %d needs %zu bytes of scratch, the static array holds %zu",
                         d.nx, d.ny, d.nz, need, (size_t)MM_NOALLOC_SCRATCH_BYTES);
 
-  // Set-up, once per device, with that device current.
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MM_NOALLOC_MAX_DEVICES) {
-    cudaGetLastError();
-    return noalloc_fail(MM_ECUDA, "mm_heff_noalloc: no usable current device");
-  }
+  // Set-up (the scratch's device address), once per device and context.
   unsigned char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p) {
-        cudaGetLastError();
-        return noalloc_fail(MM_ECUDA, "mm_heff_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      }
-      g_scratch_addr[dev] = p;
-    }
-    base = (unsigned char*)g_scratch_addr[dev];
-  }
-  int* flags = (int*)base;   // kernels' error flags (a bounded wait that gave up sets flags[1])
+  if (int rc = mm_noalloc_scratch(&base)) return rc;
+  int* flags = (int*)base;   // kernels' error flags, read by mm_noalloc_status
   float* Kh = (float*)(base + fl_b);
   float2* tw = (float2*)(base + fl_b + kh_b);
   double2* Kc = (double2*)(base + fl_b + kh_b + tw_b);
   float2* S = (float2*)(base + fl_b + kh_b + tw_b);
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(flags, 0, 4 * sizeof(int), s) != cudaSuccess)
-    return noalloc_fail(MM_ECUDA, "mm_heff_noalloc: clearing the flags failed");
 
   k_noalloc_twiddles<<<(2 * Lmax + 255) / 256, 256, 0, s>>>(tw, Lmax);
   if (cudaGetLastError() != cudaSuccess) return noalloc_fail(MM_ECUDA, "mm_heff_noalloc: twiddle launch failed");
@@ -146,5 +188,26 @@ extern "C" int mm_heff_noalloc(const int grid[3], double delta, double Ms, doubl
   if (launch_field_eval(d, ph, a, tw, S, Kh, flags, s) < 0)
     return noalloc_fail(MM_ECUDA, "mm_heff_noalloc: field kernels failed to launch: %s",
                         cudaGetErrorString(cudaGetLastError()));
+  return MM_OK;
+}
+
+extern "C" int mm_noalloc_status(void* stream) {
+  unsigned char* base = nullptr;
+  if (int rc = mm_noalloc_scratch(&base)) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  int h[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(h, base, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    const cudaError_t e = cudaGetLastError();
+    return noalloc_fail(MM_ECUDA, "mm_noalloc_status: reading the flags failed: %s", cudaGetErrorString(e));
+  }
+  if (h[0] || h[1]) {
+    if (cudaMemsetAsync(base, 0, sizeof h, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+      const cudaError_t e = cudaGetLastError();
+      return noalloc_fail(MM_ECUDA, "mm_noalloc_status: clearing the flags failed: %s", cudaGetErrorString(e));
+    }
+    if (h[1]) return noalloc_fail(MM_ETIMEOUT, "mm_heff_noalloc: a bounded wait inside a kernel gave up");
+    return noalloc_fail(MM_ENONFINITE, "mm_heff_noalloc: a kernel flagged a non-finite value");
+  }
   return MM_OK;
 }

@@ -72,6 +72,8 @@ _SIGNATURES = {
     "mm_last_error": (ctypes.c_char_p, [_P]),
     "mm_heff_noalloc": (_I, [ctypes.POINTER(_I), _D, _D, _D, _D, ctypes.POINTER(_D), _I, _P, _P,
                              ctypes.c_uint, _P]),
+    "mm_noalloc_status": (_I, [_P]),
+    "mm_fp32_probe": (_I, [_I, _I, _P, ctypes.POINTER(_D)]),
     "mm_noalloc_last_error": (ctypes.c_char_p, []),
     "mm_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), _D, _D, _D, _D, _D, _D, ctypes.POINTER(Opts)]),
     "mm_batch_destroy": (None, [_P]),
@@ -311,6 +313,46 @@ def heff_noalloc(grid, delta, Ms, A, Ku, b_ext, m, H, mask: int = TERM_ALL, self
     if rc != MM_OK:
         raise MMError(rc, L.mm_noalloc_last_error().decode())
     return H
+
+
+def fp32_probe_tflops(packed: bool, iters: int = 1 << 16, reps: int = 5):
+    """Measured FP32 rate (TFLOP/s) of the mm_fp32_probe kernel on the current device:
+    the best of `reps` CUDA-event-timed launches after one warm-up launch."""
+    import torch
+    L = lib()
+    s = torch.cuda.current_stream()
+    fl = _D()
+    best = 0.0
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        rc = L.mm_fp32_probe(1 if packed else 0, int(iters), s.cuda_stream, ctypes.byref(fl))
+        e1.record(s)
+        if rc != MM_OK:
+            raise MMError(rc, "mm_fp32_probe failed")
+        torch.cuda.synchronize()
+        if r:
+            best = max(best, fl.value / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
+
+
+def noalloc_status(stream=None):
+    """mm_noalloc_status: synchronise the stream and raise MMError if a kernel of an
+    earlier heff_noalloc call on this device flagged a failure (flags are cleared)."""
+    import torch
+    L = lib()
+    s = torch.cuda.current_stream() if stream is None else stream
+    rc = L.mm_noalloc_status(s.cuda_stream)
+    if rc != MM_OK:
+        raise MMError(rc, L.mm_noalloc_last_error().decode())
+
+
+def noalloc_selftest_wait_timeout(polls: int = 1000):
+    """mm_selftest_wait_timeout(NULL, polls): a kernel on the legacy default stream
+    whose bounded wait runs out and sets heff_noalloc's timeout flag."""
+    rc = lib().mm_selftest_wait_timeout(None, int(polls))
+    if rc != MM_OK:
+        raise MMError(rc, lib().mm_noalloc_last_error().decode())
 
 
 class _FilmView(Solver):

@@ -32,4 +32,32 @@ def gpu_heff(solver, m_dev_np, mask):
     return H.cpu().numpy().astype(np.float64)
 
 
-__all__ = ["rel_l2", "make_solver", "make_film", "gpu_heff", "to_device", "to_xyz"]
+def sample_cells(grid, n_random, seed):
+    """Target cells for sampled parity: the 8 corners, the midpoints of the 12 edges,
+    the centres of the 6 faces (so both z faces are covered), and n_random seeded
+    cells; (i, j, k) in paper order."""
+    nx, ny, nz = grid
+    pick = lambda n: sorted({0, n // 2, n - 1})
+    cells = set()
+    for i in pick(nx):
+        for j in pick(ny):
+            for k in pick(nz):
+                # corners (three end values), edge midpoints (one centre), face centres (two)
+                centres = (i == nx // 2) + (j == ny // 2) + (k == nz // 2)
+                if centres <= 2:
+                    cells.add((i, j, k))
+    rng = np.random.default_rng(seed)
+    while len(cells) < 26 + n_random:
+        cells.add((int(rng.integers(nx)), int(rng.integers(ny)), int(rng.integers(nz))))
+    return sorted(cells)
+
+
+def per_cell_rel(Hg_dev, Ho_cells, cells):
+    """max over the sampled cells of |H_gpu - H_oracle| / |H_oracle| (vector norms)."""
+    Hgc = np.array([[Hg_dev[a, k, j, i] for a in range(3)] for (i, j, k) in cells])
+    num = np.linalg.norm(Hgc - Ho_cells, axis=1)
+    den = np.linalg.norm(Ho_cells, axis=1)
+    return float((num / den).max())
+
+
+__all__ = ["sample_cells", "per_cell_rel", "rel_l2", "make_solver", "make_film", "gpu_heff", "to_device", "to_xyz"]

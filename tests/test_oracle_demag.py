@@ -129,3 +129,18 @@ def test_demag_at_cells_uniform_box_matches_surface_charges(a):
         p = np.array(cell, float) + 0.5
         Hq = Ms * _surface_charge_field(lo, hi, p, a)
         assert np.abs(H[q] - Hq).max() < 1e-9 * Ms
+
+
+@pytest.mark.parametrize("self_term", [True, False])
+def test_demag_at_cells_with_a_precomputed_tensor(self_term):
+    # the sliced route (tensor given) is the per-cell route and the brute force
+    grid = (6, 5, 3)
+    m = _random_unit(grid, 9)
+    K = demag_tensor(*grid, self_term=self_term)
+    cells = [(0, 0, 0), (5, 4, 2), (2, 3, 1), (5, 0, 0), (0, 4, 2)]
+    Hk = demag_at_cells(m, 8e5, cells, K=K)
+    Hc = demag_at_cells(m, 8e5, cells, self_term=self_term)
+    Hd = demag_direct(m, 8e5, K)
+    ref = np.array([Hd[(slice(None),) + c] for c in cells])
+    assert np.abs(Hk - Hc).max() <= 1e-13 * np.abs(Hc).max()
+    assert np.abs(Hk - ref).max() <= 1e-13 * np.abs(ref).max()

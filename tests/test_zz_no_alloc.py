@@ -1,12 +1,16 @@
 """mm_heff_noalloc: the context-free, allocation-free effective field.
 
-Some callers cannot call cudaMalloc -- code running during CUDA-graph stream
-capture, or code whose device memory belongs to another allocator -- so the
-library offers an entry point whose scratch is a static device array.  Its
-result must equal mm_heff of a context created with the same parameters and
-holding the same state, within the parity tolerance of the other tests
-(relative L2 <= 1e-5), on two calls in a row (the second call reuses the
-scratch the first one left behind).
+Some callers cannot call cudaMalloc -- a plug-in whose host application owns
+the GPU's memory pool, code running where a caching allocator already holds
+the free device memory, a loop that cannot take the device-wide
+synchronisation of an allocation -- so the library offers an entry point whose
+scratch is a static device array.  Its result must equal mm_heff of a context
+created with the same parameters and holding the same state, within the
+parity tolerance of the other tests (relative L2 <= 1e-5), on calls in a row
+that reuse the scratch earlier calls left behind, including a repeat of the
+first case after a different grid has overwritten the array.  The kernels'
+error flags are read back by mm_noalloc_status; a wait that runs out on
+purpose (the wait self-test) must be reported there and cleared.
 
 This file is collected last so that a run stopped at the first failure has
 already run every other test; it also passes alone in a fresh process.
@@ -41,19 +45,43 @@ def _reference(grid, delta, Ms, A, Ku, b, m_np, mask, self_term):
     return H, m
 
 
-def test_noalloc_matches_mm_heff_twice():
+def test_noalloc_matches_mm_heff_on_calls_in_a_row():
     import torch
-    from paper_1501_07293_b300.solver import TERM_ALL, TERM_DEMAG, heff_noalloc
+    from paper_1501_07293_b300.solver import TERM_ALL, TERM_DEMAG, heff_noalloc, noalloc_status
     cases = [((40, 10, 3), 5e-9, 8e5, 1.3e-11, 5e4, (0.01, -0.02, 0.005), TERM_ALL, True, 1),
              ((24, 33, 2), 4e-9, 8e5, 1.3e-11, 0.0, (0.0, 0.0, 0.01), TERM_DEMAG, False, 2)]
+    refs = []
     for grid, delta, Ms, A, Ku, b, mask, self_term, seed in cases:
         m_np = inputs.random_state(grid, seed)
-        H_ref, m = _reference(grid, delta, Ms, A, Ku, b, m_np, mask, self_term)
+        refs.append(_reference(grid, delta, Ms, A, Ku, b, m_np, mask, self_term))
+    # case 1, case 2, then case 1 again over the bytes case 2 left in the scratch
+    for q in (0, 1, 0):
+        grid, delta, Ms, A, Ku, b, mask, self_term, _ = cases[q]
+        H_ref, m = refs[q]
         H = torch.full_like(H_ref, float("nan"))
         heff_noalloc(grid, delta, Ms, A, Ku, b, m, H, mask, self_term)
-        torch.cuda.synchronize()
+        noalloc_status()   # synchronises; no kernel flagged anything
         assert torch.isfinite(H).all()
         assert _rel(H, H_ref) <= TOL, (grid, _rel(H, H_ref))
+
+
+def test_noalloc_reports_a_wait_that_ran_out():
+    import torch
+    from paper_1501_07293_b300.solver import (MM_ETIMEOUT, TERM_ALL, MMError, heff_noalloc,
+                                              noalloc_selftest_wait_timeout, noalloc_status)
+    noalloc_status()
+    noalloc_selftest_wait_timeout(2000)   # sets the scratch's timeout flag, no fault
+    with pytest.raises(MMError) as e:
+        noalloc_status(torch.cuda.default_stream())
+    assert e.value.code == MM_ETIMEOUT
+    noalloc_status()                      # the flag was cleared
+    grid = (16, 8, 2)
+    m_np = inputs.random_state(grid, 3)
+    H_ref, m = _reference(grid, 4e-9, 8e5, 1.3e-11, 0.0, (0, 0, 0.01), m_np, TERM_ALL, True)
+    H = torch.zeros_like(H_ref)
+    heff_noalloc(grid, 4e-9, 8e5, 1.3e-11, 0.0, (0, 0, 0.01), m, H)
+    noalloc_status()
+    assert _rel(H, H_ref) <= TOL
 
 
 def test_noalloc_refuses_grids_beyond_the_scratch():
