@@ -185,3 +185,131 @@ template <int L>
 struct TeamOf {
   static constexpr int v = (L / 8) >= 32 ? 32 : ((L / 8) >= 1 ? (L / 8) : 1);
 };
+
+// ---------------------------------------------------------------------------
+// Register-resident transforms.  One lane holds N <= 32 values of a sequence in
+// registers; reg_fft is an in-place radix-2 decimation-in-frequency transform
+// whose twiddles are compile-time powers of W_32, leaving X[k] in v[brev(k)].
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int brev(int x, int bits) {
+  int r = 0;
+  for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1) << (bits - 1 - i);
+  return r;
+}
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+
+// cos(2 pi k / 32) and sin(2 pi k / 32) for an integer k (quarter-wave values)
+__host__ __device__ constexpr float cos32(int k) {
+  const float q[9] = {1.0f, 0.980785280403230449f, 0.923879532511286756f, 0.831469612302545237f,
+                      0.707106781186547524f, 0.555570233019602225f, 0.382683432365089772f,
+                      0.195090322016128268f, 0.0f};
+  k &= 31;
+  return k <= 8 ? q[k] : (k <= 16 ? -q[16 - k] : (k <= 24 ? -q[k - 16] : q[32 - k]));
+}
+__host__ __device__ constexpr float sin32(int k) { return cos32(k - 8); }
+
+// x * exp(DIR 2 pi i k / 32); k is a compile-time constant after unrolling, so the
+// quarter turns cost no multiplication
+template <int DIR>
+__device__ __forceinline__ float2 mul_w32(float2 x, int k) {
+  k &= 31;
+  if (k == 0) return x;
+  if (k == 16) return make_float2(-x.x, -x.y);
+  if (k == 8) return cquarter<DIR>(x);
+  if (k == 24) return cquarter<-DIR>(x);
+  return cmul(x, make_float2(cos32(k), DIR < 0 ? -sin32(k) : sin32(k)));
+}
+
+// ZH: the upper half of the input is zero (the first stage then only twiddles).
+template <int N, int DIR, bool ZH = false>
+__device__ __forceinline__ void reg_fft(float2 (&v)[N]) {
+  static_assert(N >= 2 && N <= 32 && (N & (N - 1)) == 0, "register transform of 2..32 values");
+#pragma unroll
+  for (int len = N; len >= 2; len >>= 1) {
+    const int h = len >> 1;
+#pragma unroll
+    for (int s = 0; s < N; s += len) {
+#pragma unroll
+      for (int j = 0; j < h; ++j) {
+        const float2 a = v[s + j], b = v[s + j + h];
+        if (ZH && len == N) {
+          v[s + j + h] = mul_w32<DIR>(a, j * (32 / len));
+        } else {
+          v[s + j] = cadd(a, b);
+          v[s + j + h] = mul_w32<DIR>(csub(a, b), j * (32 / len));
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Two-pass transform of a row of L = 16 R2 values in shared memory (R2 = 16 or
+// 32), Cooley-Tukey with L = 16 x R2:
+//   pass 1: lane l (0 <= l < R2) transforms x[l + R2 j], j < 16, in registers,
+//           multiplies result k1 by W_L^(l k1) and stores it at k1 (R2 + 1) + l
+//           (one spare slot per R2 values: the reads of pass 2 hit 16
+//           different banks);
+//   pass 2: lane k1 (0 <= k1 < 16) transforms the R2 values k1 (R2 + 1) + l
+//           and stores X[k1 + 16 k2] at its natural position.
+// Two shared-memory round trips instead of log8(L); every access is free of
+// bank conflicts.  In place: the lanes of a row read everything before any of
+// them writes (__syncwarp).  Inputs at positions >= nin are zeros (not read),
+// outputs at positions >= nout are not written; ZH: nin <= L / 2 (the upper
+// half of every pass-1 sequence is zero).
+// ---------------------------------------------------------------------------
+template <int R2, int DIR, bool ZH, int NR = 1>
+__device__ __forceinline__ void fft2_pass1(float2* const (&row)[NR], const bool (&act)[NR], int l, int nin,
+                                           const float2 (&tw)[16]) {
+  float2 v[NR][16];   // NR rows at once (independent chains)
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int n = l + R2 * j;
+      v[r][j] = make_float2(0.f, 0.f);
+      if (!(ZH && j >= 8) && act[r] && n < nin) v[r][j] = row[r][n];
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < NR; ++r) reg_fft<16, DIR, ZH>(v[r]);
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (act[r]) {
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) {
+        const float2 x = v[r][brev(k1, 4)];
+        row[r][k1 * (R2 + 1) + l] = k1 ? cmul(x, tw[k1]) : x;
+      }
+    }
+  }
+}
+
+template <int R2, int DIR>
+__device__ __forceinline__ void fft2_pass2(float2* row, bool act, int k1, int nout) {
+  float2 v[R2];
+#pragma unroll
+  for (int l = 0; l < R2; ++l) v[l] = act ? row[k1 * (R2 + 1) + l] : make_float2(0.f, 0.f);
+  __syncwarp();
+  reg_fft<R2, DIR>(v);
+  if (act) {
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int n = k1 + 16 * k2;
+      if (n < nout) row[n] = v[brev(k2, ilog2c(R2))];
+    }
+  }
+}
+
+// Pass-1 twiddles of lane l: tw[k] = W_L^(l k) (forward table twL[m] =
+// exp(-2 pi i m / L)), conjugated for the inverse.
+template <int L, int DIR>
+__device__ __forceinline__ void fft2_twiddles(float2 (&tw)[16], int l, const float2* __restrict__ twL) {
+  tw[0] = make_float2(1.f, 0.f);
+#pragma unroll
+  for (int k = 1; k < 16; ++k) {
+    const float2 w = __ldg(twL + ((l * k) & (L - 1)));
+    tw[k] = DIR < 0 ? w : cconj(w);
+  }
+}

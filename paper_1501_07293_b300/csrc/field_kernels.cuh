@@ -321,6 +321,53 @@ struct YzLayout {
   static constexpr int RS = PY + (PADS ? PY / 16 : 0) + 2;   // even: rows stay 16-byte aligned
 };
 
+// The y transforms of the 3 nz rows of a column by the two-pass transform of
+// fft.cuh (py = 256, 512).  Warp w owns rows p = w + nwarps i; pass 1 takes them
+// one per warp (R2 = 32) or two per warp (R2 = 16), pass 2 two per warp (one
+// per half-warp).  before_row(p) runs (all lanes of the row's group) before
+// pass 1 reads row p; after_pair(p, act) runs (all lanes) after pass 2 of the
+// half-warp's row p (act: the half-warp had a row).
+template <int PY, int DIR, typename Before, typename After>
+__device__ __forceinline__ void yz_rows_fft2(float2* buf, int NP, int nin, int nout, const float2* __restrict__ twY,
+                                             Before before_row, After after_pair) {
+  constexpr int RS = YzLayout<PY>::RS;
+  constexpr int R2 = PY / 16;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int half = lane >> 4, k1 = lane & 15;
+  const int nmine = warp < NP ? (NP - warp + nwarps - 1) / nwarps : 0;
+  {
+    float2 tw[16];
+    fft2_twiddles<PY, DIR>(tw, lane & (R2 - 1), twY);
+    if constexpr (R2 == 32) {   // a whole warp on each row
+      for (int i = 0; i < nmine; ++i) {
+        const int p = warp + nwarps * i;
+        before_row(p);
+        float2* const rows[1] = {buf + p * RS};
+        const bool act[1] = {true};
+        fft2_pass1<32, DIR, (DIR < 0)>(rows, act, lane, nin, tw);
+      }
+    } else {                    // a row per half-warp
+      for (int i = 0; i < nmine; i += 2) {
+        const int ii = i + half;
+        const bool a1 = ii < nmine;
+        const int p = warp + nwarps * (a1 ? ii : i);
+        if (a1) before_row(p);
+        float2* const rows[1] = {buf + p * RS};
+        const bool act[1] = {a1};
+        fft2_pass1<R2, DIR, (DIR < 0)>(rows, act, lane & (R2 - 1), nin, tw);
+      }
+    }
+  }
+  __syncwarp();
+  for (int i = 0; i < nmine; i += 2) {
+    const int ii = i + half;
+    const bool act = ii < nmine;
+    const int p = warp + nwarps * (act ? ii : i);
+    fft2_pass2<R2, DIR>(buf + p * RS, act, k1, nout);
+    after_pair(p, act);
+  }
+}
+
 // Split-precision variants (PREC = MM_SPLIT_BF16 / MM_SPLIT_FP16) replace the
 // FP32 direct sum of step 3 by zs::zprod_split on the tensor cores; the DFT
 // operands follow the rows in shared memory.
@@ -331,6 +378,10 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   constexpr int T = TeamOf<PY>::v;
   constexpr int PADS = YzLayout<PY>::PADS;
   constexpr int RS = YzLayout<PY>::RS;
+  // py = 256, 512: the two-pass y transform (natural order between the
+  // transforms); other sizes: the Stockham passes (padded order in between)
+  constexpr bool FFT2 = (PY == 256 || PY == 512);
+  constexpr int ZPADS = FFT2 ? 0 : PADS;   // layout the z product reads
   extern __shared__ __align__(16) float2 sm[];
   float2* tws = sm;        // exp(-2 pi i m / PY), m < PY
   float2* buf = sm + PY;   // [3 nz][RS]
@@ -413,9 +464,15 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   const unsigned mask = team_mask<T>(lane);
   bool arrived = true;
   if (grouped) {   // transforms start on the rows that have landed
-    for (int p = team; p < NP; p += nteams) {
-      arrived = mbar_wait_bounded(&bar[p / rpg], 0) && arrived;
-      if (PY > 1) team_fft_io<PY, T, -1, 1, 0, PADS, PADS>(buf + p * RS, t, mask, tws, ny, PY);
+    if constexpr (FFT2) {
+      yz_rows_fft2<PY, -1>(buf, NP, ny, PY, twY,
+                           [&](int p) { arrived = mbar_wait_bounded(&bar[p / rpg], 0) && arrived; },
+                           [](int, bool) {});
+    } else {
+      for (int p = team; p < NP; p += nteams) {
+        arrived = mbar_wait_bounded(&bar[p / rpg], 0) && arrived;
+        if (PY > 1) team_fft_io<PY, T, -1, 1, 0, PADS, PADS>(buf + p * RS, t, mask, tws, ny, PY);
+      }
     }
   } else if (bulk) {
     arrived = mbar_wait_bounded(&bar[0], 0);
@@ -435,8 +492,12 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   }
   if constexpr (PREC != 0) zs::fence_after();
   if (PY > 1 && !grouped) {
-    for (int p = team; p < NP; p += nteams)
-      team_fft_io<PY, T, -1, 1, 0, PADS, PADS>(buf + p * RS, t, mask, tws, ny, PY);
+    if constexpr (FFT2) {
+      yz_rows_fft2<PY, -1>(buf, NP, ny, PY, twY, [](int) {}, [](int, bool) {});
+    } else {
+      for (int p = team; p < NP; p += nteams)
+        team_fft_io<PY, T, -1, 1, 0, PADS, PADS>(buf + p * RS, t, mask, tws, ny, PY);
+    }
     __syncthreads();
   }
   // Product of eq. 14 along z (see zprod).
@@ -445,7 +506,7 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
     static_assert(PY >= 128 && PY % 128 == 0, "split z product: chunks of 128 ky");
     const uint32_t tb = tbase;
     uint32_t phase = 0;
-    const bool ok = zs::zprod_split<PY, NZM, PREC, PADS>(buf, RS, nz, PY, d.hy, d.Kt + (long long)kx * d.hy * (NZM + 1) * 6,
+    const bool ok = zs::zprod_split<PY, NZM, PREC, ZPADS>(buf, RS, nz, PY, d.hy, d.Kt + (long long)kx * d.hy * (NZM + 1) * 6,
                                                          Bsm, tb, &mbar, phase, flag);
     if (!ok) mbar_wait_bounded(&mbar, phase);   // MMAs still in flight get one more bounded wait
     zs::fence_before();
@@ -453,31 +514,49 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
     if ((threadIdx.x >> 5) == 0) zs::tmem_dealloc(tb, 512);
     if (!ok) return;
   } else if constexpr (NZM > 16)
-    zprod_column_chunked<NZM, (PY > 1 ? PADS : 0)>(buf, RS, PY, nz, Kh + (long long)kx * d.hy * 6 * nz, PY,
-                                                   KyIdentity());
+    zprod_column_chunked<NZM, (PY > 1 ? ZPADS : 0)>(buf, RS, PY, nz, Kh + (long long)kx * d.hy * 6 * nz, PY,
+                                                    KyIdentity());
   else if (PY > 1)
-    zprod_column<NZM, PADS>(buf, RS, PY, nz, Kh + (long long)kx * d.hy * 6 * nz, d.hy, PY, KyIdentity());
+    zprod_column<NZM, ZPADS>(buf, RS, PY, nz, Kh + (long long)kx * d.hy * 6 * nz, d.hy, PY, KyIdentity());
   else
     zprod_column<NZM, 0>(buf, RS, PY, nz, Kh + (long long)kx * 6 * nz * d.hy, d.hy, PY, KyIdentity());
   __syncthreads();
   if (grouped) {
     // each team stores its own rows: every lane orders its writes of the row
     // before the bulk engine's reads, then the team's first lane issues the copy
-    for (int p = team; p < NP; p += nteams) {
-      if (PY > 1) team_fft_io<PY, T, 1, 1, PADS, PADS, 0>(buf + p * RS, t, mask, tws, PY, ny);
-      fence_proxy_async_smem();
-      __syncwarp(mask);
-      if (t == 0) {
-        bulk_s2g(Sk + (long long)p * ny, buf + p * RS, ny * sizeof(float2));
-        bulk_commit();
+    if constexpr (FFT2) {
+      bool issued = false;
+      yz_rows_fft2<PY, 1>(buf, NP, PY, ny, twY, [](int) {}, [&](int p, bool act) {
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (act && (threadIdx.x & 15) == 0) {
+          bulk_s2g(Sk + (long long)p * ny, buf + p * RS, ny * sizeof(float2));
+          bulk_commit();
+          issued = true;
+        }
+      });
+      if (issued) bulk_wait_read_all();   // the rows stay valid until read
+    } else {
+      for (int p = team; p < NP; p += nteams) {
+        if (PY > 1) team_fft_io<PY, T, 1, 1, PADS, PADS, 0>(buf + p * RS, t, mask, tws, PY, ny);
+        fence_proxy_async_smem();
+        __syncwarp(mask);
+        if (t == 0) {
+          bulk_s2g(Sk + (long long)p * ny, buf + p * RS, ny * sizeof(float2));
+          bulk_commit();
+        }
       }
+      if (t == 0) bulk_wait_read_all();   // the rows stay valid until read
     }
-    if (t == 0) bulk_wait_read_all();   // the rows stay valid until read
     return;
   }
   if (PY > 1) {
-    for (int p = team; p < NP; p += nteams)
-      team_fft_io<PY, T, 1, 1, PADS, PADS, 0>(buf + p * RS, t, mask, tws, PY, ny);
+    if constexpr (FFT2) {
+      yz_rows_fft2<PY, 1>(buf, NP, PY, ny, twY, [](int) {}, [](int, bool) {});
+    } else {
+      for (int p = team; p < NP; p += nteams)
+        team_fft_io<PY, T, 1, 1, PADS, PADS, 0>(buf + p * RS, t, mask, tws, PY, ny);
+    }
     __syncthreads();
   }
   if (bulk) {
