@@ -582,7 +582,12 @@ def b300_arm(args, w):
     from paper_1501_07293_b300.solver import Solver
 
     mat = w.mat
+    # set-up: the FP64 tensor (eq. 10/11 near the source, its multipole series
+    # beyond 12 cells) and its FP64 transforms; mm_create synchronises
+    torch.cuda.synchronize()
+    t_setup0 = time.perf_counter()
     s = Solver(w.grid, w.delta, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma, precision=args.precision)
+    setup_ms = 1e3 * (time.perf_counter() - t_setup0)
     s.set_field(w.b_ext)
     m0 = inputs.workload_state(w)
     m0_dev = torch.from_numpy(m0).cuda()
@@ -730,6 +735,7 @@ def b300_arm(args, w):
             "step_fraction_of_hbm_roofline": (4 * meth["eval"] * K / t_max / 1e9) / peak,   # per GPU
             "step_bytes_per_cell": 4 * meth["eval"] / ncell,
             "fp32_peak": fp32,
+            "setup_ms": setup_ms,
             "wall_s_timed_region": t_wall,
             "clocks": clk.summary(),
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,

@@ -80,9 +80,15 @@ typedef struct {
                        one extra launch per step); read with mm_get_series.  The paper
                        writes <m> every 1000 steps (script of Appendix A).  0: off.      */
   void* stream;     /* cudaStream_t the context enqueues on; NULL = legacy default       */
+  const char* tune_cache;   /* path of a JSON file of launch shapes recorded by the
+                       autotuner (paper_1501_07293_b300.tune.autotune): mm_create
+                       applies the y/z route and ky block recorded for this grid's
+                       padded size and precision, as mm_set_tuning would.  NULL, a
+                       missing file or a missing entry keep the built-in choice.     */
 } mm_opts;
 
-/* Fill *opts with the defaults: MM_FP32, MM_RK4, self_term 1, obs_every 0, NULL stream. */
+/* Fill *opts with the defaults: MM_FP32, MM_RK4, self_term 1, obs_every 0, NULL stream,
+ * no tune cache. */
 void mm_default_opts(mm_opts* opts);
 
 /*
@@ -276,6 +282,21 @@ long long mm_launch_count(const mm_ctx* ctx);
  * reported by mm_noalloc_status.
  */
 int mm_selftest_wait_timeout(mm_ctx* ctx, unsigned polls);
+
+/*
+ * The demagnetising tensor K_ab of eq. 10/11 (in units where delta = 1; the
+ * tensor is scale free) at n (1 .. 2^20) integer offsets, evaluated on the
+ * current device in FP64 exactly as the set-up of mm_create does it: the
+ * eight-corner sums of eq. 10/11 within 12 cells of the source, beyond that
+ * the multipole series of the same tensor (the field of a uniformly
+ * magnetised cube, expanded in powers of 1/|n|; the paper has no
+ * counterpart), whose truncation error is below ~1e-15 relative where the
+ * corner sums lose ~eps |n|^3 to cancellation.  offsets: host, n triples
+ * (I, J, K); out: host, n x 6 doubles (xx, yy, zz, xy, xz, yz).  The self
+ * offset gives -I/3.  Synchronises; allocates two small device buffers.
+ * MM_EINVAL / MM_ENOMEM / MM_ECUDA.
+ */
+int mm_tensor_eval(const int* offsets, int n, double* out);
 
 /*
  * Peak-rate probe of the FP32 pipes (measurement only; the paper has no

@@ -14,6 +14,10 @@ centre of the target cell, with
     Kxz = -1/(4 pi) sum s log(y + r)                 (eq. 11 permuted)
     Kyz = -1/(4 pi) sum s log(x + r)                 (eq. 11 permuted)
 
+``tensor_at_mp`` evaluates the same sums with mpmath at 50 digits: the
+reference for offsets far from the source, where the FP64 corner sums lose
+~eps |n|^3 of relative accuracy to cancellation.
+
 The printed sum limit "i = 1 to 1" of eq. 10/11 is read as i in {0, 1}, the
 range the paper's own tensor listing loops over.  The coordinates are
 half-integers times delta, so no denominator vanishes.
@@ -106,3 +110,34 @@ def box_point_tensor(lo, hi, p):
                 out[1, 2] -= s * np.log(x + r)
     out[1, 0], out[2, 0], out[2, 1] = out[0, 1], out[0, 2], out[1, 2]
     return out / (4.0 * np.pi)
+
+
+def tensor_at_mp(I, J, Kk, dps=50):
+    """Eq. 10/11 at one integer offset, evaluated with mpmath at `dps` significant
+    digits (the same eight-corner sums as tensor_at, without FP64 cancellation:
+    far from the source the corner terms are O(1) while their sum is O(|n|^-3)).
+
+    Returns a dict component -> Python float (the correctly rounded value).
+    """
+    import mpmath
+    with mpmath.workdps(dps):
+        half = mpmath.mpf(1) / 2
+        acc = {c: mpmath.mpf(0) for c in COMPONENTS}
+        for i in (0, 1):
+            for j in (0, 1):
+                for k in (0, 1):
+                    s = -1 if (i + j + k) % 2 else 1
+                    x = mpmath.mpf(I) + i - half
+                    y = mpmath.mpf(J) + j - half
+                    z = mpmath.mpf(Kk) + k - half
+                    r = mpmath.sqrt(x * x + y * y + z * z)
+                    acc["xx"] += s * mpmath.atan(y * z / (x * r))
+                    acc["yy"] += s * mpmath.atan(x * z / (y * r))
+                    acc["zz"] += s * mpmath.atan(y * x / (z * r))
+                    acc["xy"] += s * mpmath.log(z + r)
+                    acc["xz"] += s * mpmath.log(y + r)
+                    acc["yz"] += s * mpmath.log(x + r)
+        pref = 1 / (4 * mpmath.pi)
+        out = {c: float(pref * acc[c]) for c in ("xx", "yy", "zz")}
+        out.update({c: float(-pref * acc[c]) for c in ("xy", "xz", "yz")})
+    return out

@@ -5,9 +5,19 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
+
+// NVTX range around an entry point (visible in Nsight timelines; free when no
+// tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 static char g_create_err[512] = "";
 
@@ -95,6 +105,7 @@ extern "C" void mm_default_opts(mm_opts* o) {
   o->self_term = 1;
   o->obs_every = 0;
   o->stream = nullptr;
+  o->tune_cache = nullptr;
 }
 
 static void free_ctx(mm_ctx* c) {
@@ -117,6 +128,39 @@ extern "C" void mm_destroy(mm_ctx* c) {
   free_ctx(c);
 }
 
+// Launch shape recorded for this context in a tune cache (JSON written by the
+// Python autotuner): the record under "<px>x<py>x<nz>:<precision>" holds integer
+// fields "yz_route" and "zt_block".  Returns 1 and the values if found.
+static int read_tune_cache(const char* path, const mm_ctx* c, int* route, int* block) {
+  FILE* f = fopen(path, "rb");
+  if (!f) return 0;
+  std::string txt;
+  char buf[4096];
+  size_t n;
+  while ((n = fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, n);
+  fclose(f);
+  const char* prec = c->d.prec == MM_SPLIT_BF16 ? "split_bf16" : (c->d.prec == MM_SPLIT_FP16 ? "split_fp16" : "fp32");
+  char key[96];
+  snprintf(key, sizeof key, "\"%dx%dx%d:%s\"", c->d.px, c->d.py, c->d.nz, prec);
+  size_t at = txt.find(key);
+  if (at == std::string::npos) return 0;
+  at = txt.find('{', at);
+  if (at == std::string::npos) return 0;
+  size_t end = at;
+  for (int depth = 0; end < txt.size(); ++end) {   // the record's closing brace
+    if (txt[end] == '{') ++depth;
+    else if (txt[end] == '}' && --depth == 0) break;
+  }
+  const std::string rec = txt.substr(at, end - at);
+  auto field = [&](const char* name, int* out) {
+    const size_t k = rec.find(name);
+    if (k == std::string::npos) return false;
+    const size_t colon = rec.find(':', k);
+    return colon != std::string::npos && sscanf(rec.c_str() + colon + 1, "%d", out) == 1;
+  };
+  return field("\"yz_route\"", route) && field("\"zt_block\"", block) ? 1 : 0;
+}
+
 #define ALLOC(ptr, bytes)                                                                       \
   do {                                                                                          \
     if (cudaMalloc((void**)&(ptr), (bytes)) != cudaSuccess) {                                   \
@@ -128,6 +172,7 @@ extern "C" void mm_destroy(mm_ctx* c) {
 
 extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double Ms, double A, double Ku,
                          double alpha, double gamma, const mm_opts* opts) {
+  NvtxRange nvtx_("mm_create");
   if (!out) return mm_fail(nullptr, MM_EINVAL, "out is NULL");
   *out = nullptr;
   if (!grid) return mm_fail(nullptr, MM_EINVAL, "grid is NULL");
@@ -221,6 +266,15 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double M
   if (rc != MM_OK) {
     snprintf(g_create_err, sizeof g_create_err, "%s", c->err);
     goto fail;
+  }
+  if (o.tune_cache) {   // launch shapes recorded by the autotuner for this size
+    int route = 0, block = 0;
+    if (read_tune_cache(o.tune_cache, c, &route, &block) && mm_set_tuning(c, route, block) != MM_OK) {
+      snprintf(g_create_err, sizeof g_create_err, "%s", c->err);
+      rc = MM_EINVAL;
+      goto fail;
+    }
+    c->opts.tune_cache = nullptr;   // the path need not outlive mm_create
   }
   {
     // m = (1, 0, 0)
@@ -340,6 +394,7 @@ static void stage_drive(mm_ctx* c, StageArgs& a, int s, double dt) {
 }
 
 extern "C" int mm_heff(mm_ctx* c, float* H, unsigned mask) {
+  NvtxRange nvtx_("mm_heff");
   if (!c) return MM_EINVAL;
   if (!H) return mm_fail(c, MM_EINVAL, "mm_heff: H is NULL");
   if (mask & ~(unsigned)MM_TERM_ALL) return mm_fail(c, MM_EINVAL, "mm_heff: bad term mask 0x%x", mask);
@@ -456,6 +511,7 @@ static int build_graphs(mm_ctx* c, double dt) {
 }
 
 extern "C" int mm_step(mm_ctx* c, int n, double dt) {
+  NvtxRange nvtx_("mm_step");
   if (!c) return MM_EINVAL;
   if (n < 0) return mm_fail(c, MM_EINVAL, "mm_step: n = %d < 0", n);
   if (!(dt > 0) || dt > 1e-6) return mm_fail(c, MM_EINVAL, "mm_step: dt = %g s out of range (0, 1e-6]", dt);
@@ -479,6 +535,7 @@ extern "C" int mm_step(mm_ctx* c, int n, double dt) {
 }
 
 extern "C" int mm_step_timed(mm_ctx* c, int n, double dt, double ms_out[3]) {
+  NvtxRange nvtx_("mm_step_timed");
   if (!c) return MM_EINVAL;
   if (!ms_out) return mm_fail(c, MM_EINVAL, "mm_step_timed: ms_out is NULL");
   if (n < 0) return mm_fail(c, MM_EINVAL, "mm_step_timed: n = %d < 0", n);
@@ -526,6 +583,7 @@ extern "C" int mm_step_timed(mm_ctx* c, int n, double dt, double ms_out[3]) {
       a.m_out = outp[s4];
       stage_drive(c, a, s4, dt);
       for (int part = 1; part < 3; ++part) {
+        NvtxRange pass_(part == 1 ? "y/z pass" : "x pass + update");
         const int nl = launch_field_part(c->d, ph, a, c->tw, c->S, c->Kh, c->dflag, c->stream, part);
         if (nl < 0) {
           rc = mm_fail(c, MM_ECUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -585,6 +643,7 @@ static int run_reduce(mm_ctx* c, double* host) {
 }
 
 extern "C" int mm_energy(mm_ctx* c, double E[5]) {
+  NvtxRange nvtx_("mm_energy");
   if (!c) return MM_EINVAL;
   if (!E) return mm_fail(c, MM_EINVAL, "mm_energy: E is NULL");
   double r[9];
@@ -596,6 +655,7 @@ extern "C" int mm_energy(mm_ctx* c, double E[5]) {
 }
 
 extern "C" int mm_observables(mm_ctx* c, double out[5]) {
+  NvtxRange nvtx_("mm_observables");
   if (!c) return MM_EINVAL;
   if (!out) return mm_fail(c, MM_EINVAL, "mm_observables: out is NULL");
   double r[9];

@@ -31,7 +31,7 @@ class MMError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("integrator", ctypes.c_int), ("self_term", ctypes.c_int),
-                ("obs_every", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("obs_every", ctypes.c_int), ("stream", ctypes.c_void_p), ("tune_cache", ctypes.c_char_p)]
 
 
 class Segment(ctypes.Structure):
@@ -74,6 +74,7 @@ _SIGNATURES = {
                              ctypes.c_uint, _P]),
     "mm_noalloc_status": (_I, [_P]),
     "mm_fp32_probe": (_I, [_I, _I, _P, ctypes.POINTER(_D)]),
+    "mm_tensor_eval": (_I, [_P, _I, _P]),
     "mm_noalloc_last_error": (ctypes.c_char_p, []),
     "mm_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), _D, _D, _D, _D, _D, _D, ctypes.POINTER(Opts)]),
     "mm_batch_destroy": (None, [_P]),
@@ -134,6 +135,8 @@ class Solver:
         o.self_term = 1 if self_term else 0
         o.precision = {"fp32": MM_FP32, "split_bf16": MM_SPLIT_BF16, "split_fp16": MM_SPLIT_FP16}[precision]
         o.obs_every = int(obs_every)
+        # launch shapes an earlier autotune stored for this size (applied by mm_create)
+        o.tune_cache = None if tune_cache is None else os.fsencode(tune_cache)
         with torch.cuda.device(self.device):
             s = torch.cuda.current_stream() if stream is None else stream
             o.stream = s.cuda_stream
@@ -147,9 +150,6 @@ class Solver:
         self.ctx = ctx
         self._L = L
         self.precision = precision
-        if tune_cache is not None:   # launch shapes an earlier autotune stored for this size
-            from .tune import apply_cached
-            apply_cached(self, tune_cache)
 
     # -- helpers --------------------------------------------------------------
     def _check(self, rc: int):
@@ -313,6 +313,17 @@ def heff_noalloc(grid, delta, Ms, A, Ku, b_ext, m, H, mask: int = TERM_ALL, self
     if rc != MM_OK:
         raise MMError(rc, L.mm_noalloc_last_error().decode())
     return H
+
+
+def tensor_eval(offsets) -> np.ndarray:
+    """mm_tensor_eval: the FP64 tensor (xx, yy, zz, xy, xz, yz) at integer offsets
+    (an (n, 3) array of I, J, K), as the set-up kernel evaluates it."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32).reshape(-1, 3))
+    out = np.zeros((off.shape[0], 6), dtype=np.float64)
+    rc = lib().mm_tensor_eval(off.ctypes.data, int(off.shape[0]), out.ctypes.data)
+    if rc != MM_OK:
+        raise MMError(rc, "mm_tensor_eval failed")
+    return out
 
 
 def fp32_probe_tflops(packed: bool, iters: int = 1 << 16, reps: int = 5):

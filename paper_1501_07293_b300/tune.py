@@ -7,7 +7,8 @@ is faster depends on the grid: the number of kx columns against the 148 SMs,
 the planes per column, the block's shared memory.  ``autotune`` times every
 candidate on the solver's own film with CUDA events (``mm_step_timed``, the y/z
 class of kernels), keeps the fastest, and records it under the padded size in a
-JSON file; ``apply_cached`` (also ``Solver(..., tune_cache=path)``) reuses it.
+JSON file; ``mm_opts.tune_cache`` (``Solver(..., tune_cache=path)``) makes
+``mm_create`` apply it, and ``apply_cached`` applies it to an existing solver.
 The state, the clock and the step count of the solver are restored afterwards.
 Results are identical for every candidate; only the time differs.
 """

@@ -103,3 +103,38 @@ def test_thin_film_and_long_rod_limits():
     assert abs(plate[2, 2] + 1.0) < 1e-3 and abs(plate[0, 0]) < 1e-3
     rod = box_point_tensor(np.array([-5e3, -0.5, -0.5]), np.array([5e3, 0.5, 0.5]), p)
     assert abs(rod[0, 0]) < 1e-6 and abs(rod[1, 1] + 0.5) < 1e-6 and abs(rod[2, 2] + 0.5) < 1e-6
+
+
+def test_mp_tensor_equals_fp64_near_the_source():
+    # near the source the 50-digit and FP64 corner sums agree to the FP64 sums'
+    # cancellation bound, a few eps |n|^3 relative
+    from oracle.tensor import tensor_at, tensor_at_mp
+    for off in [(0, 0, 0), (1, 0, 0), (1, 2, 0), (2, 1, 3), (3, 3, 1), (0, 4, 2), (5, 1, 1)]:
+        mp = tensor_at_mp(*off)
+        f = tensor_at(*off)
+        scale = max(abs(v) for v in mp.values())
+        n = np.sqrt(sum(v * v for v in off))
+        for c in mp:
+            assert abs(float(f[c]) - mp[c]) <= (1e-15 + 4e-16 * n ** 3) * scale, (off, c)
+
+
+def test_mp_tensor_self_term_trace_and_far_field_rate():
+    from oracle.tensor import tensor_at_mp
+    mp = tensor_at_mp(0, 0, 0)
+    assert abs(mp["xx"] + 1 / 3) < 1e-16 and abs(mp["xy"]) < 1e-16
+    # trace zero off the source, to the precision of the 50-digit sums
+    for off in [(40, 25, 3), (300, 7, 15), (1000, 500, 60)]:
+        t = tensor_at_mp(*off)
+        assert abs(t["xx"] + t["yy"] + t["zz"]) <= 1e-15 * max(abs(v) for v in t.values()), off
+
+    # the gap to the point dipole (3 n n^T - I) / (4 pi |n|^3) falls as |n|^-4
+    def gap(n):
+        t = tensor_at_mp(*n)
+        r = np.sqrt(sum(v * v for v in n))
+        u = np.array(n, float) / r
+        dip = (3 * np.outer(u, u) - np.eye(3)) / (4 * np.pi * r ** 3)
+        m = np.array([[t["xx"], t["xy"], t["xz"]], [t["xy"], t["yy"], t["yz"]], [t["xz"], t["yz"], t["zz"]]])
+        return np.abs(m - dip).max() / np.abs(dip).max()
+    for n in [(20, 13, 7), (50, 30, 10)]:
+        ratio = gap(n) / gap(tuple(2 * v for v in n))
+        assert 14.0 < ratio < 18.0, (n, ratio)
