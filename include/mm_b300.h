@@ -287,11 +287,11 @@ int mm_selftest_wait_timeout(mm_ctx* ctx, unsigned polls);
  * The demagnetising tensor K_ab of eq. 10/11 (in units where delta = 1; the
  * tensor is scale free) at n (1 .. 2^20) integer offsets, evaluated on the
  * current device in FP64 exactly as the set-up of mm_create does it: the
- * eight-corner sums of eq. 10/11 within 12 cells of the source, beyond that
+ * eight-corner sums of eq. 10/11 within 9 cells of the source, beyond that
  * the multipole series of the same tensor (the field of a uniformly
  * magnetised cube, expanded in powers of 1/|n|; the paper has no
- * counterpart), whose truncation error is below ~1e-15 relative where the
- * corner sums lose ~eps |n|^3 to cancellation.  offsets: host, n triples
+ * counterpart), whose truncation error is below ~3e-14 relative (~1e-15 beyond
+ * 12 cells) where the corner sums lose ~eps |n|^3 to cancellation.  offsets: host, n triples
  * (I, J, K); out: host, n x 6 doubles (xx, yy, zz, xy, xz, yz).  The self
  * offset gives -I/3.  Synchronises; allocates two small device buffers.
  * MM_EINVAL / MM_ENOMEM / MM_ECUDA.
@@ -321,9 +321,16 @@ const char* mm_last_error(const mm_ctx* ctx);
  * Batches of independent films (e.g. one film per point of a field sweep),
  * advanced together.  The paper runs one film; a batch applies the same
  * per-film method (every entry point above, through mm_batch_film) to many
- * films of uneven size with few launches: films with equal padded sizes share
- * one launch per kernel, and the groups run as parallel branches of one CUDA
- * graph per step.  RK4 only.
+ * films of uneven size.  Two schedules of an RK4 step, each replayed from a
+ * captured CUDA graph:
+ *   persistent (default when every film has px 32..512, py 16..256 and
+ *     nz <= 4): one kernel launch per step whose CTAs take the y/z columns and
+ *     x tiles of all films from one device work queue; an item waits (bounded)
+ *     only for the earlier items of its own film, so films of different sizes
+ *     share the SMs inside the launch;
+ *   grouped: films with equal padded sizes share one launch per kernel, and
+ *     the groups run as parallel branches of the step graph.
+ * RK4 only.
  */
 typedef struct mm_batch mm_batch;
 
@@ -360,6 +367,25 @@ int mm_batch_group_count(const mm_batch* b);
 
 /* Kernels enqueued by the batch's own launches so far. */
 long long mm_batch_launch_count(const mm_batch* b);
+
+/* Schedule of the batch's steps: 1 persistent, 0 grouped.  MM_EUNSUPPORTED if
+ * some film has no body in the persistent kernel.  The next step re-captures. */
+int mm_batch_set_schedule(mm_batch* b, int persistent);
+int mm_batch_get_schedule(const mm_batch* b);
+
+/* Block until the batch's stream is idle; MM_ETIMEOUT if a bounded wait inside a
+ * batched kernel gave up since the last call (the flag is cleared). */
+int mm_batch_sync(mm_batch* b);
+
+/*
+ * Self-test of the persistent kernel's bounded dependency waits (the paper has
+ * no counterpart): one launch of the persistent kernel in which film 0's items
+ * wait for a progress count nothing reaches and give up after `polls` (1 ..
+ * 2^20) polls; no item does its work, so every film keeps its state.  The next
+ * mm_batch_sync returns MM_ETIMEOUT; the batch stays usable.  MM_EUNSUPPORTED
+ * when the batch cannot run the persistent kernel.
+ */
+int mm_batch_selftest_wait_timeout(mm_batch* b, unsigned polls);
 
 /* Last failure of this batch ("" if none); NULL gives the last create failure. */
 const char* mm_batch_last_error(const mm_batch* b);

@@ -1,12 +1,17 @@
 // Many independent films of uneven size advanced together (a field sweep: one
 // film per applied field).  Every film has its own context (its buffers,
-// transformed tensor and twiddles); the batch groups the films by padded sizes
-// (px, py) and z-product width, and one RK4 step becomes, per group, four
-// stages of two batched launches (k_yz, k_x over all films of the group).  The
-// groups are independent, so one step is captured as a CUDA graph with one
-// parallel branch per group.  A film whose max |dm/dt| (recorded by the first
-// stage of every step) falls below a tolerance can be switched off: its CTAs
-// return at once.
+// transformed tensor and twiddles).  Two schedules of a step:
+//   persistent (the default when every film has a body in it): one launch of
+//     kb_persist (field_inst_persist.cu) per RK4 step, whose CTAs take the y/z
+//     columns and x tiles of all films from one work queue, each item waiting
+//     on its own film's progress counter only;
+//   grouped: the films are grouped by padded sizes (px, py) and z-product
+//     width, and a step is, per group, four stages of two batched launches
+//     (kb_yz, kb_x over the films of the group), one parallel graph branch per
+//     group.
+// Either way a step is replayed from a captured CUDA graph.  A film whose max
+// |dm/dt| (recorded by the first stage of every step) falls below a tolerance
+// can be switched off: its work is skipped.
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -28,6 +33,13 @@ struct BatchGroup {
 
 struct mm_batch {
   int nf = 0;
+  int schedule = 0;               // 1 persistent, 0 grouped
+  int persist_ok = 0;             // every film has a body in the persistent kernel
+  int* yz_off = nullptr;          // persistent plan: prefix sums of kx columns / x tiles (device)
+  int* x_off = nullptr;
+  int n_yz = 0, n_x = 0;
+  int* next = nullptr;            // work counter, then per-film done counters (device)
+  unsigned* done = nullptr;
   std::vector<mm_ctx*> film;
   std::vector<BatchFilm> host;
   BatchFilm* dev = nullptr;
@@ -73,6 +85,9 @@ static void free_batch(mm_batch* b) {
   cudaFree(b->dev);
   cudaFree(b->maxdmdt);
   cudaFree(b->flag);
+  cudaFree(b->yz_off);
+  cudaFree(b->x_off);
+  cudaFree(b->next);
   for (auto s : b->side) cudaStreamDestroy(s);
   for (auto e : b->join) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -169,6 +184,29 @@ extern "C" int mm_batch_create(mm_batch** out, int nfilms, const int* grids, dou
     cudaMemcpy(g.map_yz, myz.data(), sizeof(int2) * myz.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(g.map_x, mx.data(), sizeof(int2) * mx.size(), cudaMemcpyHostToDevice);
   }
+  // the persistent plan: item offsets of every film (y/z columns, x tiles)
+  b->persist_ok = 1;
+  for (int f = 0; f < nfilms; ++f) b->persist_ok = b->persist_ok && persist_supported(b->film[f]->d);
+  if (b->persist_ok) {
+    std::vector<int> yo(nfilms + 1, 0), xo(nfilms + 1, 0);
+    for (int f = 0; f < nfilms; ++f) {
+      yo[f + 1] = yo[f] + (b->film[f]->d.hx + kPersistGYZ - 1) / kPersistGYZ;
+      xo[f + 1] = xo[f] + (persist_x_tiles(b->film[f]->d) + kPersistGX - 1) / kPersistGX;
+    }
+    b->n_yz = yo[nfilms];
+    b->n_x = xo[nfilms];
+    if (cudaMalloc(&b->yz_off, sizeof(int) * yo.size()) != cudaSuccess ||
+        cudaMalloc(&b->x_off, sizeof(int) * xo.size()) != cudaSuccess ||
+        cudaMalloc(&b->next, sizeof(int) * (1 + (size_t)nfilms)) != cudaSuccess) {
+      cudaGetLastError();
+      free_batch(b);
+      return bfail(nullptr, MM_ENOMEM, "persistent plan: allocation failed");
+    }
+    b->done = reinterpret_cast<unsigned*>(b->next + 1);
+    cudaMemcpy(b->yz_off, yo.data(), sizeof(int) * yo.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->x_off, xo.data(), sizeof(int) * xo.size(), cudaMemcpyHostToDevice);
+  }
+  b->schedule = b->persist_ok;
   b->host.resize(nfilms);
   b->side.resize(b->groups.size());
   b->join.resize(b->groups.size());
@@ -235,6 +273,33 @@ static int enqueue_group_step(mm_batch* b, const BatchGroup& g, cudaStream_t s, 
   return 0;
 }
 
+static PersistPlan persist_plan(mm_batch* b, double dt, int nsteps) {
+  PersistPlan p;
+  p.F = b->dev;
+  p.yz_off = b->yz_off;
+  p.x_off = b->x_off;
+  p.nf = b->nf;
+  p.n_yz = b->n_yz;
+  p.n_x = b->n_x;
+  p.gyz = kPersistGYZ;
+  p.gx = kPersistGX;
+  p.nsteps = nsteps;
+  p.next = b->next;
+  p.done = b->done;
+  p.flag = b->flag;
+  p.spin_limit = 1u << 26;   // about a second of polls (64 ns naps) before a wait gives up
+  p.blocked_film = -1;
+  p.dry = 0;
+  p.dt = (float)dt;
+  return p;
+}
+
+// One persistent launch (counters cleared first): 3 graph nodes per step.
+static int enqueue_persist(mm_batch* b, const PersistPlan& p, cudaStream_t s) {
+  if (cudaMemsetAsync(b->next, 0, sizeof(int) * (1 + (size_t)b->nf), s) != cudaSuccess) return -1;
+  return launch_persist(p, s) < 0 ? -1 : 0;
+}
+
 static int build_graph(mm_batch* b, double dt) {
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
@@ -244,6 +309,20 @@ static int build_graph(mm_batch* b, double dt) {
   cudaGraph_t graph;
   long long nk = 0;
   BCK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  if (b->schedule) {   // persistent: one kernel for every film's step
+    const int r = enqueue_persist(b, persist_plan(b, dt, 1), cap);
+    cudaError_t e = cudaStreamEndCapture(cap, &graph);
+    if (r != 0 || e != cudaSuccess) {
+      cudaGetLastError();
+      return bfail(b, MM_ECUDA, "batch graph capture failed (%s)", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bfail(b, MM_ECUDA, "batch graph instantiate failed: %s", cudaGetErrorString(e));
+    b->graph_dt = dt;
+    b->graph_nodes = 1;
+    return MM_OK;
+  }
   int r = cudaEventRecord(b->fork, cap) == cudaSuccess ? 0 : -1;
   for (size_t g = 1; g < b->groups.size() && r == 0; ++g)
     r = cudaStreamWaitEvent(b->side[g], b->fork, 0) == cudaSuccess ? 0 : -1;
@@ -330,5 +409,55 @@ extern "C" int mm_batch_max_dmdt(mm_batch* b, float* out) {
   if (!b || !out) return MM_EINVAL;
   BCK(cudaMemcpyAsync(out, b->maxdmdt, sizeof(float) * b->nf, cudaMemcpyDeviceToHost, b->stream));
   BCK(cudaStreamSynchronize(b->stream));
+  return MM_OK;
+}
+
+extern "C" int mm_batch_set_schedule(mm_batch* b, int persistent) {
+  if (!b) return MM_EINVAL;
+  if (persistent != 0 && persistent != 1) return bfail(b, MM_EINVAL, "mm_batch_set_schedule: 0 or 1");
+  if (persistent && !b->persist_ok)
+    return bfail(b, MM_EUNSUPPORTED, "the persistent kernel has no body for some film of this batch "
+                                     "(px 32..512, py 16..256, nz <= 4)");
+  if (persistent != b->schedule) {
+    b->schedule = persistent;
+    if (b->graph) {
+      cudaStreamSynchronize(b->stream);
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+  }
+  return MM_OK;
+}
+
+extern "C" int mm_batch_get_schedule(const mm_batch* b) { return b ? b->schedule : -1; }
+
+extern "C" int mm_batch_sync(mm_batch* b) {
+  if (!b) return MM_EINVAL;
+  int h[4];
+  BCK(cudaMemcpyAsync(h, b->flag, sizeof h, cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  if (h[0] || h[1]) {
+    BCK(cudaMemsetAsync(b->flag, 0, sizeof h, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    if (h[1]) return bfail(b, MM_ETIMEOUT, "a bounded wait inside a batched kernel gave up");
+    return bfail(b, MM_ENONFINITE, "a batched kernel flagged a non-finite value");
+  }
+  return MM_OK;
+}
+
+extern "C" int mm_batch_selftest_wait_timeout(mm_batch* b, unsigned polls) {
+  if (!b) return MM_EINVAL;
+  if (!b->persist_ok) return bfail(b, MM_EUNSUPPORTED, "the self-test runs the persistent kernel");
+  if (polls < 1 || polls > (1u << 20)) return bfail(b, MM_EINVAL, "mm_batch_selftest_wait_timeout: polls out of range");
+  std::vector<int> all(b->nf, 1);
+  int r = sync_descriptors(b, &all);
+  if (r != MM_OK) return r;
+  PersistPlan p = persist_plan(b, 1e-15, 1);
+  p.blocked_film = 0;   // film 0's items wait for a count nothing reaches
+  p.spin_limit = polls;
+  p.dry = 1;            // no item does its work: the films keep their states
+  if (enqueue_persist(b, p, b->stream) != 0)
+    return bfail(b, MM_ECUDA, "self-test launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  b->launches++;
   return MM_OK;
 }

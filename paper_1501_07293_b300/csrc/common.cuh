@@ -169,6 +169,36 @@ struct BatchFilm {
   int active;       // 0: the film's CTAs return at once
 };
 
+// One persistent launch over every film of a batch (field_inst_persist.cu):
+// a work queue of items in the order (stage of the launch, pass, film, tile),
+// pass 0 = the y/z columns of every film, pass 1 = the x tiles of every film.
+// An item of film f waits (bounded polls) until film f has finished all its
+// earlier items, counted in done[f]; items are taken in queue order, so every
+// wait is for items already taken by running CTAs.
+struct PersistPlan {
+  const BatchFilm* F;
+  const int* yz_off;     // [nf + 1] prefix sums of the films' y/z items (gyz kx columns each)
+  const int* x_off;      // [nf + 1] prefix sums of the films' x items (gx row tiles each)
+  int nf, n_yz, n_x;     // films; y/z items and x items of one stage
+  int gyz, gx;           // kx columns per y/z item, row tiles per x item
+  int nsteps;            // RK4 steps of the launch
+  int* next;             // work counter (zeroed before the launch)
+  unsigned* done;        // [nf] items finished per film (zeroed before the launch)
+  int* flag;             // error flags; [1] <- a dependency or copy wait gave up
+  unsigned spin_limit;   // polls before a dependency wait gives up
+  int blocked_film;      // self-test: this film's items wait for a count never reached (-1: none)
+  int dry;               // self-test: take and order the items, skip their work
+  float dt;
+};
+// 1 if the persistent kernel has bodies for a film of these sizes
+int persist_supported(const Dims& d);
+// x tiles of a film in the persistent kernel
+int persist_x_tiles(const Dims& d);
+// kx columns per y/z item and row tiles per x item of the persistent kernel
+static constexpr int kPersistGYZ = 16, kPersistGX = 8;
+// launch it (grid: every SM's resident CTAs); returns 1 or < 0
+int launch_persist(const PersistPlan& p, cudaStream_t s);
+
 // field.cu: one batched launch over the films of a group with equal padded sizes.
 // kind: 0 = x forward of m0, 1 = y/z + product, 2 = x inverse + RK4 stage + x forward.
 // map[i] = (film, tile) of CTA i; TY = rows per tile of the x kernels (x_batch_tile).

@@ -38,6 +38,21 @@
 #include "zsplit.cuh"
 
 
+// Loads of state that another CTA of the same launch may have written (PC: the
+// persistent batch kernel, whose items depend on one another through device
+// counters) go through L2 (ld.global.cg), never from a stale L1 line or the
+// read-only path; otherwise the read-only path (ld_ro) or a plain load (ld_rw).
+template <bool PC, typename T>
+__device__ __forceinline__ T ld_ro(const T* p) {
+  if constexpr (PC) return __ldcg(p);
+  else return __ldg(p);
+}
+template <bool PC, typename T>
+__device__ __forceinline__ T ld_rw(const T* p) {
+  if constexpr (PC) return __ldcg(p);
+  else return *p;
+}
+
 // ---------------------------------------------------------------------------
 // k_xfwd: CTA = (tile of TY rows along y, plane z, component c)
 // ---------------------------------------------------------------------------
@@ -371,7 +386,7 @@ __device__ __forceinline__ void yz_rows_fft2(float2* buf, int NP, int nin, int n
 // Split-precision variants (PREC = MM_SPLIT_BF16 / MM_SPLIT_FP16) replace the
 // FP32 direct sum of step 3 by zs::zprod_split on the tensor cores; the DFT
 // operands follow the rows in shared memory.
-template <int PY, int NZM, int PREC = 0>
+template <int PY, int NZM, int PREC = 0, bool PC = false>
 __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __restrict__ Kh,
                                         const float2* __restrict__ twY, const Dims& d, int* flag, int kx,
                                         const Tick& tk = Tick{}) {
@@ -393,7 +408,9 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   const int nz = d.nz, ny = d.ny;
   const int NP = 3 * nz;
   float2* Sk = S + (long long)kx * NP * ny;
-  const bool bulk = (ny % 2) == 0;   // rows of ny float2 are then 16-byte multiples
+  // rows of ny float2 are then 16-byte multiples; the persistent batch kernel
+  // (PC) keeps to plain loads and stores (one memory proxy, ordered by its counters)
+  const bool bulk = !PC && (ny % 2) == 0;
   const bool grouped = CAN_GROUP && bulk && d.pdl;
   // rows p of group g: g * rpg <= p < min(NP, (g + 1) * rpg)
   const int rpg = grouped ? (NP + YZ_GROUPS - 1) / YZ_GROUPS : NP;
@@ -452,7 +469,7 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
     if (bulk) {
       if (threadIdx.x == 0) issue_copies();
     } else {
-      for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) buf[(i / ny) * RS + i % ny] = Sk[i];
+      for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) buf[(i / ny) * RS + i % ny] = ld_rw<PC>(Sk + i);
     }
   }
   // first y/z pass of a step: the last warp of CTA 0 advances the field
@@ -722,6 +739,7 @@ __device__ __forceinline__ float3 llg_stage(const StageArgs& a, const Phys& ph, 
 
 // One cell given its demag field bd (tesla).  Mode 0 writes H; modes 1/2 write
 // and return the next stage / new state.
+template <bool PC = false>
 __device__ __forceinline__ float3 cell_update(const StageArgs& a, const Phys& ph, const Dims& d,
                                               int x, int y, int z, float3 bd, float* kmag = nullptr) {
   const long long N = d.N;
@@ -737,9 +755,9 @@ __device__ __forceinline__ float3 cell_update(const StageArgs& a, const Phys& ph
     float v[3][7];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      v[c][6] = __ldg(mi + cell + c * N);
+      v[c][6] = ld_ro<PC>(mi + cell + c * N);
 #pragma unroll
-      for (int q = 0; q < 6; ++q) v[c][q] = __ldg(mi + nb[q] + c * N);
+      for (int q = 0; q < 6; ++q) v[c][q] = ld_ro<PC>(mi + nb[q] + c * N);
     }
     m = make_float3(v[0][6], v[1][6], v[2][6]);
     lap.x = ((v[0][0] - m.x) + (v[0][1] - m.x)) + ((v[0][2] - m.x) + (v[0][3] - m.x)) + ((v[0][4] - m.x) + (v[0][5] - m.x));
@@ -774,8 +792,9 @@ __device__ __forceinline__ float3 cell_update(const StageArgs& a, const Phys& ph
   }
   float3 m0 = m, accv = m;
   if (a.mode == 1) {
-    m0 = make_float3(a.m0[cell], a.m0[cell + N], a.m0[cell + 2 * N]);
-    if (a.stage > 0) accv = make_float3(a.acc[cell], a.acc[cell + N], a.acc[cell + 2 * N]);
+    m0 = make_float3(ld_rw<PC>(a.m0 + cell), ld_rw<PC>(a.m0 + cell + N), ld_rw<PC>(a.m0 + cell + 2 * N));
+    if (a.stage > 0)
+      accv = make_float3(ld_rw<PC>(a.acc + cell), ld_rw<PC>(a.acc + cell + N), ld_rw<PC>(a.acc + cell + 2 * N));
   }
   float3 acc_out;
   const float3 nm = llg_stage(a, ph, m, B, m0, accv, &acc_out, kmag);
@@ -805,7 +824,7 @@ template <> struct VecOf<4> {
   __device__ static T make(const float* o) { return make_float4(o[0], o[1], o[2], o[3]); }
 };
 
-template <int V>
+template <int V, bool PC = false>
 __device__ __forceinline__ void cell_updateV(const StageArgs& a, const Phys& ph, const Dims& d, int x0, int y,
                                              int z, const float3 (&bd)[V], float3 (&nm)[V], float* kmag) {
   using Vec = VecOf<V>;
@@ -820,13 +839,13 @@ __device__ __forceinline__ void cell_updateV(const StageArgs& a, const Phys& ph,
   for (int c = 0; c < 3; ++c) {
     const float* b = a.m_in + cell + c * N;
     float sv[V + 2], vym[V], vyp[V], vzm[V], vzp[V];
-    Vec::get(__ldg(reinterpret_cast<const T*>(b)), sv + 1);
-    sv[0] = x0 > 0 ? __ldg(b - 1) : sv[1];
-    sv[V + 1] = x0 + V < d.nx ? __ldg(b + V) : sv[V];
-    Vec::get(__ldg(reinterpret_cast<const T*>(b + oym)), vym);
-    Vec::get(__ldg(reinterpret_cast<const T*>(b + oyp)), vyp);
-    Vec::get(__ldg(reinterpret_cast<const T*>(b + ozm)), vzm);
-    Vec::get(__ldg(reinterpret_cast<const T*>(b + ozp)), vzp);
+    Vec::get(ld_ro<PC>(reinterpret_cast<const T*>(b)), sv + 1);
+    sv[0] = x0 > 0 ? ld_ro<PC>(b - 1) : sv[1];
+    sv[V + 1] = x0 + V < d.nx ? ld_ro<PC>(b + V) : sv[V];
+    Vec::get(ld_ro<PC>(reinterpret_cast<const T*>(b + oym)), vym);
+    Vec::get(ld_ro<PC>(reinterpret_cast<const T*>(b + oyp)), vyp);
+    Vec::get(ld_ro<PC>(reinterpret_cast<const T*>(b + ozm)), vzm);
+    Vec::get(ld_ro<PC>(reinterpret_cast<const T*>(b + ozp)), vzp);
 #pragma unroll
     for (int j = 0; j < V; ++j) {
       const float m = sv[j + 1];
@@ -861,8 +880,8 @@ __device__ __forceinline__ void cell_updateV(const StageArgs& a, const Phys& ph,
 #pragma unroll
     for (int j = 0; j < V; ++j) { m0v[c][j] = mv[c][j]; accv[c][j] = mv[c][j]; }
     if (a.mode == 1) {
-      Vec::get(*reinterpret_cast<const T*>(a.m0 + cell + c * N), m0v[c]);
-      if (a.stage > 0) Vec::get(*reinterpret_cast<const T*>(a.acc + cell + c * N), accv[c]);
+      Vec::get(ld_rw<PC>(reinterpret_cast<const T*>(a.m0 + cell + c * N)), m0v[c]);
+      if (a.stage > 0) Vec::get(ld_rw<PC>(reinterpret_cast<const T*>(a.acc + cell + c * N)), accv[c]);
     }
   }
   float Bv[3][V], ao[3][V], no[3][V];
@@ -914,7 +933,7 @@ __device__ __forceinline__ float& rowf(float2* row, int x) {
 // TMA: the S tile arrives as two tiled tensor copies (kx 0..128 and 129..257)
 // into a staging area [kx][c][TY] (xmap: the tensor map of S), instead of
 // per-thread copies; the C2R pre-processing then reads the staging area.
-template <int HALF, int TYV = XTile<HALF>::v, bool TMA = false>
+template <int HALF, int TYV = XTile<HALF>::v, bool TMA = false, bool PC = false>
 __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float2* __restrict__ S,
                                        const float2* __restrict__ twP, const Dims& d, int TY, int fwd, int z,
                                        int y0, const CUtensorMap* xmap = nullptr) {
@@ -928,7 +947,7 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
       float2* s2 = S + ((long long)2 * d.nz + z) * d.ny + y;
       const float3 bd = make_float3(ph.c_d * s0->x, ph.c_d * s1->x, ph.c_d * s2->x);
       float km = 0.f;
-      const float3 nm = cell_update(a, ph, d, 0, y, z, bd, a.maxdmdt ? &km : nullptr);
+      const float3 nm = cell_update<PC>(a, ph, d, 0, y, z, bd, a.maxdmdt ? &km : nullptr);
       kmax = fmaxf(kmax, km);
       if (fwd) {
         *s0 = make_float2(nm.x, 0.f);
@@ -1012,8 +1031,10 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
         const int c = rest % 3, k = rest / 3;
         const int y = y0 + r;
         float2* dst = rows + (c * TY + r) * RS + pidx<PADS>(k);
-        if (y < d.ny) cp_async8(dst, S + (((long long)k * 3 + c) * d.nz + z) * d.ny + y);
-        else *dst = make_float2(0.f, 0.f);
+        const float2* src = S + (((long long)k * 3 + c) * d.nz + z) * d.ny + y;
+        if (y >= d.ny) *dst = make_float2(0.f, 0.f);
+        else if constexpr (PC) *dst = __ldcg(src);
+        else cp_async8(dst, src);
       }
       cp_async_commit();
       for (int i = threadIdx.x; i < P; i += blockDim.x) tws[i] = twP[i];
@@ -1049,7 +1070,7 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
           bd[2 * h + 1] = make_float3(ph.c_d * p0.y, ph.c_d * p1.y, ph.c_d * p2.y);
         }
         float km = 0.f;
-        cell_updateV<XV>(a, ph, d, x0, y, z, bd, nm, a.maxdmdt ? &km : nullptr);
+        cell_updateV<XV, PC>(a, ph, d, x0, y, z, bd, nm, a.maxdmdt ? &km : nullptr);
         kmax = fmaxf(kmax, km);
         if (fwd) {
 #pragma unroll
@@ -1071,7 +1092,7 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
       float& f2 = rowf<PADS>(rows + (2 * TY + r) * RS, x);
       const float3 bd = make_float3(ph.c_d * f0, ph.c_d * f1, ph.c_d * f2);
       float km = 0.f;
-      const float3 nm = cell_update(a, ph, d, x, y, z, bd, a.maxdmdt ? &km : nullptr);
+      const float3 nm = cell_update<PC>(a, ph, d, x, y, z, bd, a.maxdmdt ? &km : nullptr);
       kmax = fmaxf(kmax, km);
       if (fwd) { f0 = nm.x; f1 = nm.y; f2 = nm.z; }
     }

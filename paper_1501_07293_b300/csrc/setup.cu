@@ -4,7 +4,7 @@
 //    0 <= J < ny, 0 <= K < nz, written with the tensor's parities to the up to
 //    four positions (+-I mod px, +-J mod py) of the padded plane of K (the
 //    padding is cleared first).  Offsets are in units of delta (the tensor is
-//    scale free).  Near the source (|n| < 12 cells) the eight-corner sums of
+//    scale free).  Near the source (|n| < 9 cells) the eight-corner sums of
 //    eq. 10/11, with log(z + r) evaluated as log((x^2 + y^2) / (r - z)) when
 //    z < 0 (the same number without the cancellation of z + r).  Farther out
 //    the corner sums cancel to ~eps |n|^3 relative (a few 1e-8 at 500 cells),
@@ -127,11 +127,12 @@ __device__ void tensor_series(double x, double y, double z, int kmax, double (&v
   }
 }
 
-// Truncation order of the far-field series by distance |n| (cells): below a
-// relative truncation error of ~1e-15 (measured against a 50-digit evaluation
-// of eq. 10/11); 0 = use the corner sums.
+// Truncation order of the far-field series by distance |n| (cells): a relative
+// truncation error below ~3e-14 at 9 cells and ~1e-15 beyond 12 (measured
+// against a 50-digit evaluation of eq. 10/11), where the FP64 corner sums are
+// off by up to ~6e-13 at 9 cells; 0 = use the corner sums.
 __device__ __forceinline__ int series_order(double n2) {
-  if (n2 < 144.0) return 0;        // |n| < 12
+  if (n2 < 81.0) return 0;         // |n| < 9
   if (n2 < 400.0) return 5;        // < 20
   if (n2 < 2500.0) return 4;       // < 50
   if (n2 < 25600.0) return 3;      // < 160

@@ -85,6 +85,10 @@ _SIGNATURES = {
     "mm_batch_group_count": (_I, [_P]),
     "mm_batch_launch_count": (ctypes.c_longlong, [_P]),
     "mm_batch_last_error": (ctypes.c_char_p, [_P]),
+    "mm_batch_set_schedule": (_I, [_P, _I]),
+    "mm_batch_get_schedule": (_I, [_P]),
+    "mm_batch_sync": (_I, [_P]),
+    "mm_batch_selftest_wait_timeout": (_I, [_P, ctypes.c_uint]),
 }
 
 _lib = None
@@ -428,6 +432,20 @@ class Batch:
 
     def group_count(self) -> int:
         return int(self._L.mm_batch_group_count(self.b))
+
+    def set_schedule(self, schedule: str):
+        """'persistent' (one launch per step over every film) or 'grouped'."""
+        self._check(self._L.mm_batch_set_schedule(self.b, 1 if schedule == "persistent" else 0))
+
+    def schedule(self) -> str:
+        return "persistent" if self._L.mm_batch_get_schedule(self.b) == 1 else "grouped"
+
+    def sync(self):
+        self._check(self._L.mm_batch_sync(self.b))
+
+    def selftest_wait_timeout(self, polls: int = 1000):
+        """One persistent launch whose dependency waits run out (mm_batch_selftest_wait_timeout)."""
+        self._check(self._L.mm_batch_selftest_wait_timeout(self.b, int(polls)))
 
     def launch_count(self) -> int:
         return int(self._L.mm_batch_launch_count(self.b))
