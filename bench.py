@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-sweep and adjoint measurements")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16", "split_fp16"],
                     help="the z product of the timed steps: FP32 direct sum or the tensor-core split forms")
+    ap.add_argument("--batch-max-steps", type=int, default=20000,
+                    help="field sweep run to convergence: step cap per film (the workload's 20,000)")
     ap.add_argument("--ref-max-steps", type=int, default=8,
                     help="reference arm: at most this many oracle RK4 steps are executed and timed")
     return ap.parse_args()
@@ -277,40 +279,113 @@ def reference_arm(args, w):
 # ---------------------------------------------------------------------------
 # B300 arm
 # ---------------------------------------------------------------------------
-def bench_batched(args, steps=40, warmup=5):
-    """The field-sweep workload: 256 independent films of uneven size, RK4, one batch.
+def bench_batched(args, steps=40, warmup=5, seq_steps=20):
+    """The field-sweep workload: 256 independent films of uneven size, RK4.
+
+    * persistent vs grouped schedule: aggregate cell-steps/s over `steps` steps;
+    * the same films one context at a time (seq_steps steps each, CUDA events
+      around the steps only): the batching speed-up;
+    * the workload as specified: mm_batch_run until each film's max |dm/dt| is
+      below 1e3 rad/s (checked every 100 steps) or args.batch_max_steps steps.
     Under torchrun the films are sharded over the ranks by estimated cost (no
-    data-path collective); the value is all films' cell-steps over the slowest rank."""
+    data-path collective); values are all films' cell-steps over the slowest rank."""
     import torch
     from paper_1501_07293_b300 import inputs
     from paper_1501_07293_b300.shard import max_over_ranks, partition
-    from paper_1501_07293_b300.solver import Batch
+    from paper_1501_07293_b300.solver import Batch, Solver
     rank, world, _ = dist_info()
     films_all = inputs.film_batch()
     mine = partition([f.grid for f in films_all], world)[rank]
     films = [films_all[i] for i in mine]
     mat = inputs.BATCH_MATERIAL
-    b = Batch([f.grid for f in films], inputs.BATCH_DELTA, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma)
-    for j, f in enumerate(films):
-        b.films[j].set_field(f.b_ext)
-        b.films[j].set_m(torch.from_numpy(inputs.initial_state("tilted_x", f.grid, f.seed)).cuda())
-    b.step(warmup, inputs.BATCH_DT)
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = b.launch_count()
+    cells = sum(f.grid[0] * f.grid[1] * f.grid[2] for f in films_all)
+    peak, _ = measured_peaks()
+    step_bytes = sum(4 * method_bytes(f.grid)["eval"] for f in films_all)
+
+    def make_batch():
+        b = Batch([f.grid for f in films], inputs.BATCH_DELTA, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma)
+        for j, f in enumerate(films):
+            b.films[j].set_field(f.b_ext)
+            b.films[j].set_m(torch.from_numpy(inputs.initial_state("tilted_x", f.grid, f.seed)).cuda())
+        return b
+
+    def timed(fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn(n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1), device="cuda")
+
+    b = make_batch()
+    sched = {}
+    for name in ("persistent", "grouped"):
+        b.set_schedule(name)
+        b.step(warmup, inputs.BATCH_DT)
+        l0 = b.launch_count()
+        ms = timed(lambda n: b.step(n, inputs.BATCH_DT), steps)
+        b.sync()
+        sched[name] = {"ms_per_step": ms / steps, "value": cells * steps / (ms * 1e-3), "unit": UNIT,
+                       "gpu_launches_per_step": (b.launch_count() - l0) / steps,
+                       "hbm_frac": step_bytes / (ms / steps * 1e-3) / 1e9 / peak}
+    groups = b.group_count()
+    b.close()
+    best = "persistent" if sched["persistent"]["ms_per_step"] <= sched["grouped"]["ms_per_step"] else "grouped"
+
+    # one context at a time (the plain single-film path), the same films
+    seq_ms = 0.0
+    for f in films:
+        s = Solver(f.grid, inputs.BATCH_DELTA, mat.Ms, mat.A, mat.Ku, mat.alpha, mat.gamma)
+        s.set_field(f.b_ext)
+        s.set_m(torch.from_numpy(inputs.initial_state("tilted_x", f.grid, f.seed)).cuda())
+        s.step(3, inputs.BATCH_DT)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(seq_steps, inputs.BATCH_DT)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms += e0.elapsed_time(e1)   # local: ranks hold different numbers of films
+        s.close()
+    seq_ms = max_over_ranks(seq_ms, device="cuda")
+    seq_ms_per_step = seq_ms / seq_steps
+
+    # the workload as specified: to |dm/dt| < 1e3 rad/s or the step cap
+    b = make_batch()
+    b.set_schedule(best)
     torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    b.step(steps, inputs.BATCH_DT)
+    nsteps = b.run(args.batch_max_steps, inputs.BATCH_DT, 1e3, check_every=100)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = max_over_ranks(e0.elapsed_time(e1), device="cuda")
-    cells = sum(f.grid[0] * f.grid[1] * f.grid[2] for f in films_all)
-    out = {"workload": "256 films, nx 32..256, ny 8..128, nz 1..4, fields -50..50 mT, RK4 dt 1e-13 s",
-           "value": cells * steps / (ms * 1e-3), "unit": UNIT, "cells": cells, "steps": steps,
-           "ms_per_step": ms / steps, "groups": b.group_count(), "gpu_launches": b.launch_count() - l0,
-           "films_per_rank": len(films), "sharding": f"by film over {world} rank(s), cost-balanced",
-           "l2": "working set larger than L2 (no flush)"}
+    run_ms = max_over_ranks(e0.elapsed_time(e1), device="cuda")
+    wall = time.perf_counter() - t0
+    cell_steps = sum(f.grid[0] * f.grid[1] * f.grid[2] * n for f, n in zip(films, nsteps))
+    final_dmdt = b.max_dmdt()
     b.close()
+    srt = sorted(nsteps)
+    out = {"workload": "256 films, nx 32..256, ny 8..128, nz 1..4, fields -50..50 mT, RK4 dt 1e-13 s",
+           "cells": cells, "groups": groups, "films_per_rank": len(films),
+           "sharding": f"by film over {world} rank(s), cost-balanced",
+           "schedules": sched, "schedule_used": best,
+           "value": sched[best]["value"], "unit": UNIT, "ms_per_step": sched[best]["ms_per_step"],
+           "hbm_frac": sched[best]["hbm_frac"],
+           "bytes_model": "sum over films of 4 x the method's bytes per field evaluation (passes a1 + a2 + a3)",
+           "one_context_at_a_time": {"ms_per_step": seq_ms_per_step, "value": cells / (seq_ms_per_step * 1e-3),
+                                     "steps_timed_per_film": seq_steps},
+           "speedup_over_one_context_at_a_time": seq_ms_per_step / sched[best]["ms_per_step"],
+           "speedup_persistent_over_grouped": sched["grouped"]["ms_per_step"] / sched["persistent"]["ms_per_step"],
+           "run_to_convergence": {"tol_rad_per_s": 1e3, "check_every": 100, "max_steps": args.batch_max_steps,
+                                  "device_ms": run_ms, "wall_s": wall,
+                                  "value": cell_steps / (run_ms * 1e-3) if world == 1 else None,
+                                  "steps_min": srt[0], "steps_median": srt[len(srt) // 2], "steps_max": srt[-1],
+                                  "films_stopped_early": int(sum(1 for n in nsteps if n < args.batch_max_steps)),
+                                  "max_dmdt_at_stop_median": float(np.median(final_dmdt))},
+           "l2": "working set larger than L2 (no flush)"}
     return out
 
 def bench_adjoint(args, reps=3):
@@ -435,27 +510,68 @@ def bench_split(args, fp32_ms, steps=30, warmup=3):
                      "speedup_vs_fp32": fp32_ms / ms, "yz_ms_per_launch": kt[1] / 20,
                      "heff_rel_l2_vs_fp32": err}
         s.close()
-    # precision study
+    # precision study (512x512x8 vortex): along 20 FP32 RK4 steps, at every step's
+    # state, the FP32 and split fields against the FP64 oracle at 42 sampled cells
+    # (eq. 13 at each cell plus the eq. 5/7 exchange field; Ku and the applied
+    # field are zero), and the split fields against the FP32 field everywhere
+    from oracle import to_xyz
+    from oracle.demag import demag_at_cells
+    from oracle.exchange import exchange_field
+    from oracle.tensor import demag_tensor
     w3 = inputs.film_512x512x8()
+    nx, ny, nz = w3.grid
     m3 = torch.from_numpy(inputs.workload_state(w3)).cuda()
     f32 = Solver(w3.grid, w3.delta, w3.mat.Ms, w3.mat.A, w3.mat.Ku, w3.mat.alpha, w3.mat.gamma)
     sp = {p: Solver(w3.grid, w3.delta, w3.mat.Ms, w3.mat.A, w3.mat.Ku, w3.mat.alpha, w3.mat.gamma, precision=p)
           for p in ("split_bf16", "split_fp16")}
+    K = demag_tensor(*w3.grid, delta=w3.delta)
+    rng = np.random.default_rng(3008)
+    cells = sorted({(0, 0, 0), (nx - 1, ny - 1, nz - 1), (nx // 2, ny // 2, 0), (nx // 2, ny // 2, nz - 1),
+                    (0, ny // 2, nz // 2), (nx - 1, 0, 0)} |
+                   {(int(rng.integers(nx)), int(rng.integers(ny)), int(rng.integers(nz))) for _ in range(36)})
     f32.set_m(m3)
-    errs = {p: [] for p in sp}
+    vs_fp32 = {p: [] for p in sp}
+    vs_oracle = {p: [] for p in ["fp32"] + list(sp)}
     for step in range(20):
         state = f32.get_m()
         Hr = f32.heff(15).double()
         f32.set_m(state)
+        mo = to_xyz(state.cpu().numpy())
+        Hex = exchange_field(mo, w3.mat.Ms, w3.mat.A, w3.delta)
+        Ho = demag_at_cells(mo, w3.mat.Ms, cells, K=K) + np.array([Hex[:, i, j, k] for (i, j, k) in cells])
+        fields = {"fp32": Hr}
         for p, sv in sp.items():
             sv.set_m(state)
-            errs[p].append(float(torch.linalg.norm(sv.heff(15).double() - Hr) / torch.linalg.norm(Hr)))
+            fields[p] = sv.heff(15).double()
+            vs_fp32[p].append(float(torch.linalg.norm(fields[p] - Hr) / torch.linalg.norm(Hr)))
+        for p, H in fields.items():
+            Hc = H.cpu().numpy()
+            Hg = np.array([[Hc[a, k, j, i] for a in range(3)] for (i, j, k) in cells])
+            vs_oracle[p].append(float(np.linalg.norm(Hg - Ho) / np.linalg.norm(Ho)))
         f32.step(1, w3.dt)
-    out["precision_study_512x512x8"] = {p: {"max_heff_rel_l2": max(e), "mean_heff_rel_l2": sum(e) / len(e)}
-                                        for p, e in errs.items()}
+    out["precision_study_512x512x8"] = {
+        "steps": 20, "oracle_cells": len(cells),
+        "heff_rel_l2_vs_fp64_oracle_sampled": {p: {"per_step": e, "max": max(e)} for p, e in vs_oracle.items()},
+        "heff_rel_l2_vs_fp32_path": {p: {"max": max(e), "mean": sum(e) / len(e)} for p, e in vs_fp32.items()}}
     f32.close()
     for sv in sp.values():
         sv.close()
+    # trajectory error: 20 RK4 steps of a 128x128x8 copy of the vortex film (same
+    # material and recipe), each precision against the FP64 oracle's trajectory
+    from oracle.llg import Film
+    grid_s = (128, 128, 8)
+    ms = inputs.initial_state("vortex", grid_s, 3008)
+    film = Film(grid_s, w3.delta, w3.mat.Ms, w3.mat.A, w3.mat.Ku, w3.mat.alpha, w3.mat.gamma)
+    mo20 = film.run(to_xyz(ms), w3.dt, 20, "rk4")
+    traj = {}
+    for p in ("fp32", "split_bf16", "split_fp16"):
+        sv = Solver(grid_s, w3.delta, w3.mat.Ms, w3.mat.A, w3.mat.Ku, w3.mat.alpha, w3.mat.gamma, precision=p)
+        sv.set_m(torch.from_numpy(ms).cuda())
+        sv.step(20, w3.dt)
+        mg = to_xyz(sv.get_m().cpu().numpy())
+        traj[p] = {"max_abs_state_error_after_20_steps": float(np.abs(mg - mo20).max())}
+        sv.close()
+    out["trajectory_128x128x8_vs_fp64_oracle"] = traj
     return out
 
 

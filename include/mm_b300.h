@@ -419,7 +419,7 @@ const char* mm_batch_last_error(const mm_batch* b);
  * Cost: every call rebuilds the tensor (the FP64 eq. 10/11 kernel and two FP64
  * transforms of 6 nz px py values) before its one field evaluation, while
  * mm_heff on a context uses the tensor mm_create built once.  Measured on a
- * B300 at 128 x 128 x 4 (CUDA events): 2.54 ms per mm_heff_noalloc call
+ * B300 at 128 x 128 x 4 (CUDA events): 1.62 ms per mm_heff_noalloc call
  * against 0.023 ms per mm_heff call.
  *
  * All intermediate data lives in one file-scope static device array of
