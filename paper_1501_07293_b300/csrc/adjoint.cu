@@ -20,9 +20,16 @@
 //     and lam_k3 += dt lam_s4, lam_k2 += dt/2 lam_s3, lam_k1 += dt/2 lam_s2.
 // The trajectory is kept as checkpoints every `ckpt_every` steps; each segment
 // is recomputed once with every stage state s_i and field B_i stored, then
-// swept in reverse.
+// swept in reverse.  Per reverse step: per stage the y/z pass and the x kernel
+// in its adjoint mode, which applies L to lam_B and does the closing and
+// opening updates of the stages in the same pass (StageArgs modes 3 - 5); the
+// closing kernel of a step also starts the previous step, so only a segment's
+// last step has a separate start (k_adj_start and an x transform).  A
+// full-length segment (recomputation and sweep) is a captured graph, replayed
+// for every segment.
 #include <string.h>
 
+#include "adjoint.cuh"
 #include "common.cuh"
 
 struct AdjArgs {
@@ -33,7 +40,6 @@ struct AdjArgs {
   float* lk[3];        // cotangents of k_1, k_2, k_3
   float* lamB;         // cotangent of B at the current stage (input of the linear operator)
   float* lamloc;       // local part of the cotangent of the current stage state
-  const float* LlamB;  // L applied to lamB (tesla)
   float* gh;           // dL/dh accumulator [3][N]
   float* gku;          // dL/dKu accumulator [N]
   const float* kumap;  // per-cell Ku or null
@@ -56,69 +62,27 @@ __device__ __forceinline__ float3 xp3(float3 a, float3 b) {
 __device__ __forceinline__ float3 add3(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
 __device__ __forceinline__ float3 sc3(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
 
-__device__ __forceinline__ float3 rhs(const AdjArgs& A, float3 s, float3 B) {
-  const float3 sxB = xp3(s, B);
-  return add3(sc3(A.g1, sxB), sc3(A.g2, xp3(s, sxB)));
-}
-
-// vector-Jacobian product of f at (s, B) with cotangent lk; accumulates dL/dh, dL/dKu
-__device__ __forceinline__ void vjp_stage(const AdjArgs& A, long long i, float3 s, float3 B, float3 lk) {
-  const float3 lxs = xp3(lk, s);
-  const float3 lamB = add3(sc3(A.g1, lxs), sc3(A.g2, xp3(lxs, s)));
-  float3 loc = add3(add3(sc3(A.g1, xp3(B, lk)), sc3(A.g2, xp3(xp3(s, B), lk))), sc3(A.g2, xp3(B, lxs)));
-  const float c = A.kumap ? A.c_an_map * A.kumap[i] : A.c_an;
-  loc.x += c * lamB.x;
-  st3v(A.lamB, A.N, i, lamB);
-  st3v(A.lamloc, A.N, i, loc);
-  st3v(A.gh, A.N, i, add3(ld3v(A.gh, A.N, i), lamB));
-  A.gku[i] += A.two_over_Ms * s.x * lamB.x;
-}
-
 __global__ void k_adj_start(AdjArgs A) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.N) return;
-  float3 s[4], B[4], k[4];
+  float3 s[4], B[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     s[q] = ld3v(A.s[q], A.N, i);
     B[q] = ld3v(A.B[q], A.N, i);
-    k[q] = rhs(A, s[q], B[q]);
   }
+  const float c = A.kumap ? A.c_an_map * A.kumap[i] : A.c_an;
+  float3 lu, lamB, loc;
+  adj_step_start(A.g1, A.g2, c, A.dt, s, B, ld3v(A.lam, A.N, i), lu, lamB, loc);
   const float h = A.dt * (1.0f / 6.0f);
-  const float3 u = make_float3(s[0].x + h * (k[0].x + 2.f * k[1].x + 2.f * k[2].x + k[3].x),
-                               s[0].y + h * (k[0].y + 2.f * k[1].y + 2.f * k[2].y + k[3].y),
-                               s[0].z + h * (k[0].z + 2.f * k[1].z + 2.f * k[2].z + k[3].z));
-  const float nu = sqrtf(u.x * u.x + u.y * u.y + u.z * u.z);
-  const float inv = 1.0f / nu;
-  const float3 mn = sc3(inv, u);
-  const float3 lam = ld3v(A.lam, A.N, i);
-  const float d = mn.x * lam.x + mn.y * lam.y + mn.z * lam.z;
-  const float3 lu = sc3(inv, make_float3(lam.x - d * mn.x, lam.y - d * mn.y, lam.z - d * mn.z));
   st3v(A.lam_m, A.N, i, lu);
   st3v(A.lk[0], A.N, i, sc3(h, lu));
   st3v(A.lk[1], A.N, i, sc3(2.f * h, lu));
   st3v(A.lk[2], A.N, i, sc3(2.f * h, lu));
-  vjp_stage(A, i, s[3], B[3], sc3(h, lu));
-}
-
-// Close stage `st` + 1 (its lamloc + L lamB is the cotangent of its state), then open stage `st`.
-__global__ void k_adj_stage(AdjArgs A, int st) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
-  const float3 ls = add3(ld3v(A.lamloc, A.N, i), ld3v(A.LlamB, A.N, i));
-  st3v(A.lam_m, A.N, i, add3(ld3v(A.lam_m, A.N, i), ls));
-  const float c = (st == 2) ? A.dt : 0.5f * A.dt;   // s_4 = m + dt k_3, s_3 = m + dt/2 k_2, s_2 = m + dt/2 k_1
-  float* lkp = A.lk[st];
-  const float3 lk = add3(ld3v(lkp, A.N, i), sc3(c, ls));
-  st3v(lkp, A.N, i, lk);
-  vjp_stage(A, i, ld3v(A.s[st], A.N, i), ld3v(A.B[st], A.N, i), lk);
-}
-
-__global__ void k_adj_finish(AdjArgs A) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
-  const float3 ls = add3(ld3v(A.lamloc, A.N, i), ld3v(A.LlamB, A.N, i));
-  st3v(A.lam, A.N, i, add3(ld3v(A.lam_m, A.N, i), ls));
+  st3v(A.lamB, A.N, i, lamB);
+  st3v(A.lamloc, A.N, i, loc);
+  st3v(A.gh, A.N, i, add3(ld3v(A.gh, A.N, i), lamB));
+  A.gku[i] += A.two_over_Ms * s[3].x * lamB.x;
 }
 
 // g <- (I - m m^T) g  (the gradient with respect to the direction of the initial state)
@@ -148,6 +112,11 @@ static int grow(mm_ctx* c, float** p, size_t* cap, size_t need_floats) {
 }
 
 void mm_adjoint_free(mm_ctx* c) {
+  for (int i = 0; i < 3; ++i)
+    if (c->adj_graph[i]) {
+      cudaGraphExecDestroy(c->adj_graph[i]);
+      c->adj_graph[i] = nullptr;
+    }
   cudaFree(c->adj_ckpt);
   cudaFree(c->adj_seg);
   cudaFree(c->adj_work);
@@ -169,27 +138,26 @@ extern "C" int mm_adjoint(mm_ctx* c, int n, double dt, int ckpt_every, const flo
   const int k = ckpt_every < n ? ckpt_every : n;
   const int nseg = (n + k - 1) / k;
   int rc;
+  float* const prev[3] = {c->adj_ckpt, c->adj_seg, c->adj_work};
   if ((rc = grow(c, &c->adj_ckpt, &c->adj_ckpt_cap, (size_t)(nseg + 1) * v3)) != MM_OK) return rc;
   if ((rc = grow(c, &c->adj_seg, &c->adj_seg_cap, (size_t)(8 * k + 1) * v3)) != MM_OK) return rc;
   if ((rc = grow(c, &c->adj_work, &c->adj_work_cap, 9 * v3 + (size_t)N)) != MM_OK) return rc;
+  if (prev[0] != c->adj_ckpt || prev[1] != c->adj_seg || prev[2] != c->adj_work)
+    for (int i = 0; i < 3; ++i)
+      if (c->adj_graph[i]) {
+        cudaGraphExecDestroy(c->adj_graph[i]);
+        c->adj_graph[i] = nullptr;
+      }
   float* W = c->adj_work;
   float *lam = W, *lam_m = W + v3, *lk0 = W + 2 * v3, *lk1 = W + 3 * v3, *lk2 = W + 4 * v3;
-  float *lamB = W + 5 * v3, *lamloc = W + 6 * v3, *LlamB = W + 7 * v3, *gh = W + 8 * v3, *gku = W + 9 * v3;
+  float *lamB = W + 5 * v3, *lamloc = W + 6 * v3, *lamB2 = W + 7 * v3, *gh = W + 8 * v3, *gku = W + 9 * v3;
+  // (lamB2: the other lam_B buffer of the fused sweep, ping-pong)
   float* seg_s = c->adj_seg;                   // [k][4][3N] stage states, then [1][3N] the segment's end
+  // (the workspace addresses are baked into the segment graph: a workspace that
+  // grows is a new allocation, so the graph is dropped then)
   float* seg_B = c->adj_seg + (size_t)(4 * k + 1) * v3;   // [k][4][3N] fields
   cudaStream_t s = c->stream;
 
-  // 1. forward n steps from the current state, keeping a checkpoint every k steps
-  MM_CK(c, cudaMemcpyAsync(c->adj_ckpt, c->m0, v3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
-  for (int g = 0; g < nseg; ++g) {
-    const int len = (g + 1) * k <= n ? k : n - g * k;
-    if ((rc = mm_step(c, len, dt)) != MM_OK) return rc;
-    MM_CK(c, cudaMemcpyAsync(c->adj_ckpt + (size_t)(g + 1) * v3, c->m0, v3 * sizeof(float),
-                             cudaMemcpyDeviceToDevice, s));
-  }
-  // 2. reverse sweep
-  MM_CK(c, cudaMemcpyAsync(lam, dL_dm_final, v3 * sizeof(float), cudaMemcpyDefault, s));
-  MM_CK(c, cudaMemsetAsync(gh, 0, (v3 + N) * sizeof(float), s));
   const Phys ph = [&] {
     Phys p;
     const double Ms = c->Ms, dl = c->delta;
@@ -211,25 +179,21 @@ extern "C" int mm_adjoint(mm_ctx* c, int n, double dt, int ckpt_every, const flo
   AdjArgs A;
   memset(&A, 0, sizeof A);
   A.lam = lam; A.lam_m = lam_m; A.lk[0] = lk0; A.lk[1] = lk1; A.lk[2] = lk2;
-  A.lamB = lamB; A.lamloc = lamloc; A.LlamB = LlamB; A.gh = gh; A.gku = gku;
+  A.lamB = lamB; A.lamloc = lamloc; A.gh = gh; A.gku = gku;
   A.kumap = c->kumap; A.c_an = ph.c_an; A.c_an_map = ph.c_an_map; A.two_over_Ms = (float)(2.0 / c->Ms);
   A.g1 = ph.g1; A.g2 = ph.g2; A.dt = (float)dt; A.N = N;
   const unsigned nb = (unsigned)((N + 255) / 256);
-  StageArgs L = {};
-  L.m_in = lamB; L.H_out = LlamB; L.mode = 0; L.mask = MM_TERM_EXCHANGE | MM_TERM_DEMAG;
-  auto apply_L = [&]() -> int {
-    const int kk = launch_field_eval(c->d, lin, L, c->tw, c->S, c->Kh, c->dflag, s);
-    if (kk < 0) return mm_fail(c, MM_ECUDA, "adjoint: field kernels failed to launch");
-    c->launches += kk;
-    return MM_OK;
-  };
-  for (int g = nseg - 1; g >= 0; --g) {
-    const int len = (g + 1) * k <= n ? k : n - g * k;
-    // recompute the segment, storing every stage state and field
-    float* m_start = seg_s;
-    MM_CK(c, cudaMemcpyAsync(m_start, c->adj_ckpt + (size_t)g * v3, v3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    if (launch_xfwd(c->d, m_start, c->tw, c->S, s) < 0) return mm_fail(c, MM_ECUDA, "adjoint: x-transform launch failed");
-    c->launches++;
+  // One segment (its start state already in seg_s): recompute it storing every
+  // stage state and field, then sweep it backwards.  Enqueued on stream q;
+  // returns the kernels launched or < 0.
+  const Dims& dA = c->d;
+  // A segment's recording: from its start state in seg_s, len RK4 steps with
+  // every stage state and field stored (ticks: the steps advance the context's
+  // clock and step count, as mm_step's do).  Enqueued on stream q.
+  auto enqueue_record = [&](cudaStream_t q, int len, bool ticks, long long* nk) -> int {
+    *nk = 0;
+    if (launch_xfwd(dA, seg_s, c->tw, c->S, q) < 0) return mm_fail(c, MM_ECUDA, "adjoint: x-transform launch failed");
+    *nk += 1;
     StageArgs a = {};
     a.hmap = c->hmap; a.kumap = c->kumap; a.mode = 1; a.dt = (float)dt; a.acc = c->acc;
     for (int j = 0; j < len; ++j) {
@@ -237,34 +201,144 @@ extern "C" int mm_adjoint(mm_ctx* c, int n, double dt, int ckpt_every, const flo
       a.m0 = sj;
       for (int st = 0; st < 4; ++st) {
         a.stage = st;
+        a.tick = (ticks && st == 0) ? Tick{c->prog, dt, 0} : Tick{};
         a.m_in = sj + st * v3;
         a.m_out = st < 3 ? sj + (st + 1) * v3 : seg_s + (size_t)4 * (j + 1) * v3;
         a.B_out = seg_B + ((size_t)4 * j + st) * v3;
-        const int kk = launch_stage(c->d, ph, a, c->tw, c->S, c->Kh, c->dflag, s);
+        const int kk = launch_stage(dA, ph, a, c->tw, c->S, c->Kh, c->dflag, q);
         if (kk < 0) return mm_fail(c, MM_ECUDA, "adjoint: stage kernels failed to launch");
-        c->launches += kk;
+        *nk += kk;
       }
     }
-    // sweep the segment backwards
-    for (int j = len - 1; j >= 0; --j) {
+    return MM_OK;
+  };
+  auto enqueue_sweep = [&](cudaStream_t q, int len, long long* nk) -> int {
+    *nk = 0;
+    // the reverse sweep of the segment: one pointwise kernel starts its last step
+    // (k_adj_start), then per step and stage one y/z pass and one x kernel that
+    // applies L to lam_B, closes the stage and opens the next (mode 3); the
+    // closing kernel of a step also starts the sweep of the step before it
+    // (mode 5), except for the segment's first step (mode 4)
+    auto step_fields = [&](int j, const float** sq, const float** Bq) {
       for (int st = 0; st < 4; ++st) {
-        A.s[st] = seg_s + ((size_t)4 * j + st) * v3;
-        A.B[st] = seg_B + ((size_t)4 * j + st) * v3;
+        sq[st] = seg_s + ((size_t)4 * j + st) * v3;
+        Bq[st] = seg_B + ((size_t)4 * j + st) * v3;
       }
-      k_adj_start<<<nb, 256, 0, s>>>(A);
+    };
+    {
+      AdjArgs Aj = A;
+      step_fields(len - 1, Aj.s, Aj.B);
+      k_adj_start<<<nb, 256, 0, q>>>(Aj);
       if (cudaGetLastError() != cudaSuccess) return mm_fail(c, MM_ECUDA, "adjoint kernel launch failed");
-      c->launches++;
-      for (int st = 2; st >= 0; --st) {
-        if ((rc = apply_L()) != MM_OK) return rc;
-        k_adj_stage<<<nb, 256, 0, s>>>(A, st);
-        if (cudaGetLastError() != cudaSuccess) return mm_fail(c, MM_ECUDA, "adjoint kernel launch failed");
-        c->launches++;
-      }
-      if ((rc = apply_L()) != MM_OK) return rc;
-      k_adj_finish<<<nb, 256, 0, s>>>(A);
-      if (cudaGetLastError() != cudaSuccess) return mm_fail(c, MM_ECUDA, "adjoint kernel launch failed");
-      c->launches++;
+      *nk += 1;
     }
+    StageArgs x = {};
+    x.kumap = c->kumap;
+    x.adj_loc = lamloc; x.adj_lam_m = lam_m; x.adj_gh = gh; x.adj_gku = gku; x.adj_lam = lam;
+    x.adj_lk0 = lk0; x.adj_dt = (float)dt;
+    x.m_in = lamB;
+    if (launch_field_part(dA, lin, x, c->tw, c->S, c->Kh, c->dflag, q, 0) < 0)
+      return mm_fail(c, MM_ECUDA, "adjoint: x-transform launch failed");
+    *nk += 1;
+    float* cur = lamB;
+    for (int j = len - 1; j >= 0; --j) {
+      const float *sq[4], *Bq[4];
+      step_fields(j, sq, Bq);
+      float* const lks[3] = {lk0, lk1, lk2};
+      for (int st = 2; st >= -1; --st) {
+        x.m_in = cur;
+        x.m_out = cur == lamB ? lamB2 : lamB;
+        if (st >= 0) {
+          x.mode = 3;
+          x.adj_s = sq[st];
+          x.adj_B = Bq[st];
+          x.adj_lk = lks[st];
+          x.adj_c = st == 2 ? (float)dt : 0.5f * (float)dt;   // s_4 = m + dt k_3, s_3 = m + dt/2 k_2, s_2 = m + dt/2 k_1
+        } else if (j > 0) {
+          x.mode = 5;   // the step's start cotangent, then the previous step's start
+          step_fields(j - 1, x.adj_sq, x.adj_Bq);
+        } else {
+          x.mode = 4;   // the segment's first step: lam = lam_m + ls
+          x.m_out = nullptr;
+        }
+        for (int part = 1; part <= 2; ++part) {
+          const int kk = launch_field_part(dA, lin, x, c->tw, c->S, c->Kh, c->dflag, q, part);
+          if (kk < 0) return mm_fail(c, MM_ECUDA, "adjoint: field kernels failed to launch");
+          *nk += kk;
+        }
+        if (x.m_out) cur = x.m_out;
+      }
+    }
+    return MM_OK;
+  };
+  // full-length segments replay captured graphs (rebuilt when the segment
+  // length, dt or the context's field, damping or launch shapes changed)
+  if (c->adj_graph_len != k || c->adj_graph_dt != dt || c->adj_graph_gen != c->param_gen)
+    for (int i = 0; i < 3; ++i)
+      if (c->adj_graph[i]) {
+        cudaGraphExecDestroy(c->adj_graph[i]);
+        c->adj_graph[i] = nullptr;
+      }
+  for (int gi = 0; gi < 3; ++gi) {
+    if (c->adj_graph[gi]) continue;
+    cudaGraph_t graph;
+    long long nk = 0;
+    MM_CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int r = gi < 2 ? enqueue_record(c->cap_stream, k, gi == 1, &nk) : enqueue_sweep(c->cap_stream, k, &nk);
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (r != MM_OK || e != cudaSuccess) {
+      cudaGetLastError();
+      return r != MM_OK ? r : mm_fail(c, MM_ECUDA, "adjoint: segment capture failed: %s", cudaGetErrorString(e));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->adj_graph[gi], graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      c->adj_graph[gi] = nullptr;
+      return mm_fail(c, MM_ECUDA, "adjoint: segment graph instantiate failed: %s", cudaGetErrorString(ei));
+    }
+    c->adj_graph_nodes[gi] = nk;
+  }
+  c->adj_graph_len = k;
+  c->adj_graph_dt = dt;
+  c->adj_graph_gen = c->param_gen;
+  auto run = [&](int gi, int len) -> int {   // a full-length segment from its graph, else eagerly
+    if (len == k) {
+      MM_CK(c, cudaGraphLaunch(c->adj_graph[gi], s));
+      c->launches += c->adj_graph_nodes[gi];
+      return MM_OK;
+    }
+    long long nk = 0;
+    const int r = gi < 2 ? enqueue_record(s, len, gi == 1, &nk) : enqueue_sweep(s, len, &nk);
+    c->launches += nk;
+    return r;
+  };
+
+  // 1. forward n steps from the current state, a checkpoint every k steps; the
+  //    last segment is recorded on the way (its stage states and fields are the
+  //    first the reverse sweep needs), so it is not recomputed
+  MM_CK(c, cudaMemcpyAsync(c->adj_ckpt, c->m0, v3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  for (int g = 0; g < nseg - 1; ++g) {
+    if ((rc = mm_step(c, k, dt)) != MM_OK) return rc;
+    MM_CK(c, cudaMemcpyAsync(c->adj_ckpt + (size_t)(g + 1) * v3, c->m0, v3 * sizeof(float),
+                             cudaMemcpyDeviceToDevice, s));
+  }
+  const int len_last = n - (nseg - 1) * k;
+  MM_CK(c, cudaMemcpyAsync(seg_s, c->m0, v3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if ((rc = run(1, len_last)) != MM_OK) return rc;
+  const float* m_final = seg_s + (size_t)4 * len_last * v3;
+  MM_CK(c, cudaMemcpyAsync(c->m0, m_final, v3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  MM_CK(c, cudaMemcpyAsync(c->adj_ckpt + (size_t)nseg * v3, m_final, v3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  c->steps += len_last;
+  // 2. reverse sweep, segment by segment
+  MM_CK(c, cudaMemcpyAsync(lam, dL_dm_final, v3 * sizeof(float), cudaMemcpyDefault, s));
+  MM_CK(c, cudaMemsetAsync(gh, 0, (v3 + N) * sizeof(float), s));
+  for (int g = nseg - 1; g >= 0; --g) {
+    const int len = (g + 1) * k <= n ? k : n - g * k;
+    if (g < nseg - 1) {
+      MM_CK(c, cudaMemcpyAsync(seg_s, c->adj_ckpt + (size_t)g * v3, v3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      if ((rc = run(0, len)) != MM_OK) return rc;
+    }
+    if ((rc = run(2, len)) != MM_OK) return rc;
   }
   c->s_valid = 0;   // S was used as scratch
   // 3. outputs

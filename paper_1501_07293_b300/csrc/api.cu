@@ -359,6 +359,7 @@ extern "C" int mm_set_field(mm_ctx* c, const double b_ext[3], const float* h_map
     c->kumap = nullptr;
   }
   c->graph_valid = 0;   // kernel parameters changed: re-captured and updated in place by mm_step
+  c->param_gen++;
   return mm_prog_push_base(c);
 }
 
@@ -367,6 +368,7 @@ extern "C" int mm_set_alpha(mm_ctx* c, double alpha) {
   if (!(alpha >= 0)) return mm_fail(c, MM_EINVAL, "alpha must be >= 0");
   c->alpha = alpha;
   c->graph_valid = 0;
+  c->param_gen++;
   return mm_prog_push_base(c);
 }
 
@@ -735,6 +737,7 @@ extern "C" int mm_set_tuning(mm_ctx* c, int yz_route, int zt_block) {
   d.T = c->T;
   c->d = d;
   c->graph_valid = 0;   // the step's launches change
+  c->param_gen++;
   return MM_OK;
 }
 

@@ -78,7 +78,8 @@ struct Tick {
   int euler;
 };
 
-// One field evaluation / stage.  mode: 0 = write H_eff, 1 = RK4 stage, 2 = Euler step.
+// One field evaluation / stage.  mode: 0 = write H_eff, 1 = RK4 stage, 2 = Euler
+// step, 3 / 4 = adjoint stage / finish (below).
 struct StageArgs {
   const float* m_in;   // state the field is evaluated at (read with neighbours)
   const float* m0;     // RK4 base state
@@ -93,6 +94,28 @@ struct StageArgs {
   Tick tick;           // launch_stage: passed to its y/z launch
   const CUtensorMap* xmap;   // host: tensor map of S for the x kernel's tile loads (null: per-thread copies)
   int* flag;           // device error flags ([1] <- a bounded wait gave up); set by the launchers
+  // modes 3 / 4 (the adjoint sweep, adjoint.cu): m_in is the cotangent lam_B of
+  // the field, the kernel forms L lam_B (exchange + demag, tesla) and then
+  // closes the stage: ls = loc + L lam_B, lam_m += ls; mode 3 also opens the
+  // next stage (lk += c ls, the VJP at (s, B), loc, dL/dh, dL/dKu updated) and
+  // writes its lam_B to m_out (and, transformed along x, to S); mode 4
+  // writes lam_m + ls to adj_lam
+  const float* adj_s;  // the next stage's state and field (mode 3)
+  const float* adj_B;
+  float* adj_loc;      // local part of the stage's cotangent (read, then rewritten in mode 3)
+  float* adj_lam_m;    // running cotangent of the step's start state
+  float* adj_lk;       // cotangent of the next stage's k (mode 3)
+  float* adj_gh;       // dL/dh, dL/dKu accumulators (mode 3)
+  float* adj_gku;
+  float* adj_lam;      // mode 4 output
+  // mode 5 = mode 4 followed by the start of the previous step's sweep (the
+  // renormalisation's cotangent, lk_1..3 and the VJP of its stage 4), whose
+  // lam_B goes to m_out and, transformed along x, to S
+  const float* adj_sq[4];   // that step's stage states and fields
+  const float* adj_Bq[4];
+  float* adj_lk0;      // its k cotangents: lk_1, then lk_2, lk_3 at 3N-float strides
+  float adj_dt;
+  float adj_c;         // dt or dt/2: how the next stage's state depends on its k
   int mode;
   int stage;           // RK4 stage 0..3
   unsigned mask;       // mode 0: MM_TERM_* terms to write
@@ -133,6 +156,14 @@ struct mm_ctx {
   long long graph_nodes[2];
   long long launches;
   long long steps;
+  long long param_gen;        // bumped whenever the field, damping, program or launch shapes change
+  // adjoint: captured graphs of a full-length segment's recording (recomputed:
+  // [0], in the forward pass with the clock advancing: [1]) and reverse sweep [2]
+  cudaGraphExec_t adj_graph[3];
+  int adj_graph_len;
+  double adj_graph_dt;
+  long long adj_graph_gen;
+  long long adj_graph_nodes[3];
   // adjoint workspace (allocated by the first mm_adjoint, grown on demand)
   float* adj_ckpt;           // checkpoints [nseg + 1][3N]
   float* adj_seg;            // stage states [k][4][3N] + end state [3N], then fields [k][4][3N]

@@ -200,7 +200,8 @@ int launch_field_part(const Dims& d, const Phys& ph, const StageArgs& a, const f
   else if (part == 2) {
     StageArgs ax = a;
     ax.flag = flag;
-    e = dispatch_x(d, ph, ax, tw, S, s, a.mode != 0);
+    // modes 1, 2 (a stage), 3 and 5 (adjoint stages) transform their output along x for the next pass
+    e = dispatch_x(d, ph, ax, tw, S, s, a.mode != 0 && a.mode != 4);
   }
   if (e != cudaSuccess) return -1;
   return part == 1 ? mm_yz_launches(d) : 1;

@@ -36,6 +36,7 @@
 #include "bulk.cuh"
 #include "program.cuh"
 #include "zsplit.cuh"
+#include "adjoint.cuh"
 
 
 // Loads of state that another CTA of the same launch may have written (PC: the
@@ -784,6 +785,55 @@ __device__ __forceinline__ float3 cell_update(const StageArgs& a, const Phys& ph
     a.H_out[cell + 2 * N] = B.z * ph.inv_mu0;
     return m;
   }
+  if (a.mode >= 3) {
+    // the adjoint sweep (StageArgs): m holds lam_B, and L lam_B (exchange + demag,
+    // tesla) closes the stage whose cotangent this kernel completes
+    const float3 L = make_float3(bex.x + bd.x, bex.y + bd.y, bex.z + bd.z);
+    const float3 ls = make_float3(a.adj_loc[cell] + L.x, a.adj_loc[cell + N] + L.y, a.adj_loc[cell + 2 * N] + L.z);
+    const float3 lm = make_float3(a.adj_lam_m[cell] + ls.x, a.adj_lam_m[cell + N] + ls.y,
+                                  a.adj_lam_m[cell + 2 * N] + ls.z);
+    if (a.mode == 4) {
+      a.adj_lam[cell] = lm.x; a.adj_lam[cell + N] = lm.y; a.adj_lam[cell + 2 * N] = lm.z;
+      return m;
+    }
+    if (a.mode == 5) {   // lm is the cotangent of the previous step's end state: start its sweep
+      float3 sq[4], Bq[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        sq[q] = make_float3(a.adj_sq[q][cell], a.adj_sq[q][cell + N], a.adj_sq[q][cell + 2 * N]);
+        Bq[q] = make_float3(a.adj_Bq[q][cell], a.adj_Bq[q][cell + N], a.adj_Bq[q][cell + 2 * N]);
+      }
+      float3 lu, lamB, loc;
+      adj_step_start(ph.g1, ph.g2, can, a.adj_dt, sq, Bq, lm, lu, lamB, loc);
+      const float h = a.adj_dt * (1.0f / 6.0f);
+      a.adj_lam_m[cell] = lu.x; a.adj_lam_m[cell + N] = lu.y; a.adj_lam_m[cell + 2 * N] = lu.z;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        float* lkq = a.adj_lk0 + 3 * N * q;
+        const float f = q == 0 ? h : 2.f * h;   // lk_1 = dt/6 lu, lk_2 = lk_3 = dt/3 lu
+        lkq[cell] = f * lu.x; lkq[cell + N] = f * lu.y; lkq[cell + 2 * N] = f * lu.z;
+      }
+      a.adj_loc[cell] = loc.x; a.adj_loc[cell + N] = loc.y; a.adj_loc[cell + 2 * N] = loc.z;
+      a.adj_gh[cell] += lamB.x; a.adj_gh[cell + N] += lamB.y; a.adj_gh[cell + 2 * N] += lamB.z;
+      a.adj_gku[cell] += ph.c_an_map * sq[3].x * lamB.x;   // c_an_map = 2 / Ms
+      a.m_out[cell] = lamB.x; a.m_out[cell + N] = lamB.y; a.m_out[cell + 2 * N] = lamB.z;
+      return lamB;
+    }
+    a.adj_lam_m[cell] = lm.x; a.adj_lam_m[cell + N] = lm.y; a.adj_lam_m[cell + 2 * N] = lm.z;
+    const float3 lk = make_float3(a.adj_lk[cell] + a.adj_c * ls.x, a.adj_lk[cell + N] + a.adj_c * ls.y,
+                                  a.adj_lk[cell + 2 * N] + a.adj_c * ls.z);
+    a.adj_lk[cell] = lk.x; a.adj_lk[cell + N] = lk.y; a.adj_lk[cell + 2 * N] = lk.z;
+    // open the next stage: the VJP of eq. 2 at its recorded state and field
+    const float3 sv = make_float3(a.adj_s[cell], a.adj_s[cell + N], a.adj_s[cell + 2 * N]);
+    const float3 Bv = make_float3(a.adj_B[cell], a.adj_B[cell + N], a.adj_B[cell + 2 * N]);
+    float3 lamB, loc;
+    llg_vjp(ph.g1, ph.g2, can, sv, Bv, lk, lamB, loc);
+    a.adj_loc[cell] = loc.x; a.adj_loc[cell + N] = loc.y; a.adj_loc[cell + 2 * N] = loc.z;
+    a.adj_gh[cell] += lamB.x; a.adj_gh[cell + N] += lamB.y; a.adj_gh[cell + 2 * N] += lamB.z;
+    a.adj_gku[cell] += ph.c_an_map * sv.x * lamB.x;   // c_an_map = 2 / Ms
+    a.m_out[cell] = lamB.x; a.m_out[cell + N] = lamB.y; a.m_out[cell + 2 * N] = lamB.z;
+    return lamB;   // transformed along x by the caller for the next application of L
+  }
   const float3 B = make_float3(bex.x + ban + bd.x + bz.x, bex.y + bd.y + bz.y, bex.z + bd.z + bz.z);
   if (a.B_out) {   // recorded for the adjoint sweep
     a.B_out[cell] = B.x;
@@ -1052,7 +1102,7 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
     for (int rr = team; rr < NR; rr += nteams) team_fft<HALF, T, 1, 2, PADS>(rows + rr * RS, t, mask, tws);
     __syncthreads();
     float kmax = 0.f;
-    if (a.mode != 0 && (d.nx % XV) == 0) {
+    if ((a.mode == 1 || a.mode == 2) && (d.nx % XV) == 0) {
       // XV consecutive cells per thread (vector loads and stores)
       constexpr int Q = HALF / XV;
       for (int i = threadIdx.x; i < TY * Q; i += blockDim.x) {

@@ -153,6 +153,7 @@ extern "C" int mm_set_program(mm_ctx* c, int nseg, const mm_segment* seg) {
   c->launches++;
   c->prog_n = nseg;
   c->graph_valid = 0;   // the stage kernels switch between parameter and drive-slot inputs
+  c->param_gen++;
   return MM_OK;
 }
 

@@ -66,6 +66,25 @@ def test_adjoint_matches_oracle_16x8x1():
     assert rel_l2(gpu["ku"], to_device(gk)) <= 1e-3
 
 
+def test_adjoint_matches_oracle_16x8x1_full_500_steps():
+    # the differentiation study's small copy over its full length: 500 RK4 steps,
+    # a checkpoint every 50 (full-length segments: the captured segment graph)
+    n = 500
+    w, m0n, h, ku, gpu = _small_case(n, 50)
+    mat = w.mat
+    film = make_film(w.grid, w.delta, Ms=mat.Ms, A=mat.A, Ku=0.0, alpha=mat.alpha, gamma=mat.gamma,
+                     h_map_dev=h, ku_map_dev=ku)
+    adj = AdjointFilm(film)
+    m0x = to_xyz(m0n)
+    mf, rec = adj.forward(m0x, w.dt, n)
+    _, g = _loss_grad_final(to_device(mf))
+    gm, gh, gk = adj.backward(rec, w.dt, to_xyz(g))
+    gm = tangent_project(m0x, gm)
+    assert rel_l2(gpu["m0"], to_device(gm)) <= 1e-3
+    assert rel_l2(gpu["h"], to_device(gh)) <= 1e-3
+    assert rel_l2(gpu["ku"], to_device(gk)) <= 1e-3
+
+
 def test_adjoint_is_independent_of_checkpoint_spacing():
     ref = _small_case(12, 12)[4]
     for k in (1, 5):
