@@ -45,7 +45,9 @@ typedef enum {
   MM_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed       */
   MM_ETIMEOUT = -4,      /* a bounded device wait gave up                     */
   MM_ENONFINITE = -5,    /* a NaN or Inf was found in the state or a result   */
-  MM_EUNSUPPORTED = -6   /* valid request this build does not implement       */
+  MM_EUNSUPPORTED = -6,  /* valid request this build does not implement       */
+  MM_EBOUNDS = -7        /* bounds-check builds only: a kernel index was out of
+                            range (the access was skipped)                    */
 } mm_status;
 
 enum { MM_FP32 = 0, MM_SPLIT_BF16 = 1, MM_SPLIT_FP16 = 2 };   /* mm_opts.precision */
@@ -267,6 +269,12 @@ int mm_get_series(mm_ctx* ctx, double* out, int max_records, int* n_records);
  */
 int mm_set_tuning(mm_ctx* ctx, int yz_route, int zt_block);
 int mm_get_tuning(const mm_ctx* ctx, int* yz_route, int* zt_block);
+
+/* Build flags of the loaded library: bit 0 set for the bounds-check build
+ * (-DMM_BOUNDS_CHECK, libmm_b300_bc.so), whose kernels check the shared-memory
+ * and global indices of their stores and copies and report an out-of-range one
+ * as MM_EBOUNDS at the next synchronising call instead of performing it. */
+int mm_build_flags(void);
 
 /* Number of kernels this context has enqueued so far (graph nodes counted per replay). */
 long long mm_launch_count(const mm_ctx* ctx);

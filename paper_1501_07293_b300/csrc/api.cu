@@ -232,6 +232,7 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double M
     ALLOC(c->red, sizeof(double) * 9 * (size_t)nb);
     ALLOC(c->red_out, sizeof(double) * 16);
     ALLOC(c->dflag, sizeof(int) * 4);
+    c->d.flag = c->dflag;
     ALLOC(c->prog, sizeof(ProgState));
     if (!mm_yz_fused(c->d)) {   // the split y/z pass meets in a global buffer
       ALLOC(c->T, sizeof(float2) * (size_t)c->d.hx * 3 * c->d.nz * c->d.py);
@@ -617,8 +618,9 @@ static int check_flag(mm_ctx* c) {
   int h[4];
   MM_CK(c, cudaMemcpyAsync(h, c->dflag, sizeof h, cudaMemcpyDeviceToHost, c->stream));
   MM_CK(c, cudaStreamSynchronize(c->stream));
-  if (h[0] || h[1]) {
+  if (h[0] || h[1] || h[2]) {
     cudaMemsetAsync(c->dflag, 0, sizeof(int) * 4, c->stream);
+    if (h[2]) return mm_fail(c, MM_EBOUNDS, "bounds check: a kernel index was out of range (access skipped)");
     if (h[1]) return mm_fail(c, MM_ETIMEOUT, "a bounded wait inside a kernel gave up (bulk copy did not complete)");
     return mm_fail(c, MM_ENONFINITE, "non-finite or zero magnetisation vector found");
   }
@@ -669,6 +671,14 @@ extern "C" int mm_observables(mm_ctx* c, double out[5]) {
 }
 
 extern "C" long long mm_launch_count(const mm_ctx* c) { return c ? c->launches : -1; }
+
+extern "C" int mm_build_flags(void) {
+#ifdef MM_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
 
 extern "C" int mm_sync(mm_ctx* c) {
   if (!c) return MM_EINVAL;

@@ -19,6 +19,41 @@
 
 #include "../../include/mm_b300.h"
 
+// Bounds-check builds (-DMM_BOUNDS_CHECK, python -m paper_1501_07293_b300.build
+// --bounds-check): the kernels of the single-film path check the shared-memory
+// and global indices of their stores and bulk copies; an index out of range
+// sets flag[2] (reported as MM_EBOUNDS by the next synchronising call) and the
+// access is skipped -- no trap.  In normal builds the checks compile away.
+#ifdef MM_BOUNDS_CHECK
+static __shared__ int* mm_bc_flag_sh;   // per CTA: the flags an out-of-range index is reported to
+extern __shared__ __align__(16) unsigned char mm_bc_dyn_sm[];   // the dynamic shared memory's base
+__device__ __forceinline__ unsigned mm_bc_dyn_bytes() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ bool mm_bc(bool ok) {
+  if (!ok && mm_bc_flag_sh) atomicOr(mm_bc_flag_sh + 2, 1);
+  return ok;
+}
+#define MM_BC_ENTER(flag)                          \
+  do {                                             \
+    if (threadIdx.x == 0) mm_bc_flag_sh = (flag);  \
+    __syncthreads();                               \
+  } while (0)
+#define MM_BC(cond) mm_bc(cond)
+// n bytes at p inside the dynamic shared memory
+#define MM_BC_SMEM(p, n)                                                                              \
+  mm_bc((const unsigned char*)(p) >= mm_bc_dyn_sm &&                                                  \
+        (size_t)((const unsigned char*)(p) - mm_bc_dyn_sm) + (size_t)(n) <= (size_t)mm_bc_dyn_bytes())
+#else
+#define MM_BC_ENTER(flag) \
+  do {                    \
+  } while (0)
+#define MM_BC(cond) true
+#define MM_BC_SMEM(p, n) true
+#endif
+
 #define MM_PI 3.14159265358979323846
 #define MM_MU0 (4.0e-7 * MM_PI)
 #define MM_SERIES_CAP 65536   // records kept by the observables ring (obs_every > 0)
@@ -38,6 +73,7 @@ struct Dims {
   int route;                   // y/z pass: 0 built-in choice, 1 fused kernel, 2 split pass (mm_set_tuning)
   int ztkb;                    // split pass: ky block of the z product (0: built-in choice)
   int pdl;                     // stage kernels launched with programmatic serialization (large grids)
+  int* flag;                   // the context's device error flags (bounds-check builds report to [2])
 };
 
 // Per-cell physics constants, float32, precomputed in double on the host.

@@ -15,6 +15,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#ifndef MM_BC_SMEM
+#define MM_BC_SMEM(p, n) true   // bounds checks: see common.cuh
+#endif
+
 // Complex arithmetic on the packed FP32 pair instructions of sm_100+ (one
 // instruction per complex add; two per complex product), rounding per
 // component exactly as the scalar forms.
@@ -141,7 +145,7 @@ __device__ __forceinline__ void stockham_pass(float2* x, int t, unsigned mask, c
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int e = base + r * NS;
-        if (e < nout) x[pidx<PADW>(e)] = v[b][r];
+        if (e < nout && MM_BC_SMEM(&x[pidx<PADW>(e)], sizeof(float2))) x[pidx<PADW>(e)] = v[b][r];
       }
     }
   }
@@ -280,7 +284,7 @@ __device__ __forceinline__ void fft2_pass1(float2* const (&row)[NR], const bool 
 #pragma unroll
       for (int k1 = 0; k1 < 16; ++k1) {
         const float2 x = v[r][brev(k1, 4)];
-        row[r][k1 * (R2 + 1) + l] = k1 ? cmul(x, tw[k1]) : x;
+        if (MM_BC_SMEM(&row[r][k1 * (R2 + 1) + l], sizeof(float2))) row[r][k1 * (R2 + 1) + l] = k1 ? cmul(x, tw[k1]) : x;
       }
     }
   }
@@ -297,7 +301,7 @@ __device__ __forceinline__ void fft2_pass2(float2* row, bool act, int k1, int no
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) {
       const int n = k1 + 16 * k2;
-      if (n < nout) row[n] = v[brev(k2, ilog2c(R2))];
+      if (n < nout && MM_BC_SMEM(&row[n], sizeof(float2))) row[n] = v[brev(k2, ilog2c(R2))];
     }
   }
 }

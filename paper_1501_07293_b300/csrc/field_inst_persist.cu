@@ -83,6 +83,7 @@ __device__ __forceinline__ void persist_yz(const BatchFilm& f, int kx, int* flag
 
 __global__ void __launch_bounds__(kPersistThreads, 2) kb_persist(PersistPlan P) {
   __shared__ int s_item, s_ok;
+  MM_BC_ENTER(P.flag);
   const int per = P.n_yz + P.n_x;   // items of one stage, both passes
   const int total = per * 4 * P.nsteps;
   for (;;) {

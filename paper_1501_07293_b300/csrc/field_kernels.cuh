@@ -109,7 +109,7 @@ __device__ __forceinline__ void body_xfwd(const float* __restrict__ m, float2* _
       const float2 dif = csub(zk, zc);
       const float2 o = cmul(make_float2(dif.y, -dif.x), tws[k]);
       const float2 X = cscale(cadd(cadd(zk, zc), o), 0.5f);
-      S[(((long long)k * 3 + c) * d.nz + z) * d.ny + y] = X;
+      if (MM_BC(k < d.hx && z < d.nz && y < d.ny)) S[(((long long)k * 3 + c) * d.nz + z) * d.ny + y] = X;
     }
   }
 }
@@ -117,6 +117,7 @@ __device__ __forceinline__ void body_xfwd(const float* __restrict__ m, float2* _
 template <int HALF>
 __global__ void __launch_bounds__(512) k_xfwd(const float* __restrict__ m, float2* __restrict__ S,
                                               const float2* __restrict__ twP, Dims d, int TY) {
+  MM_BC_ENTER(d.flag);
   body_xfwd<HALF>(m, S, twP, d, TY, blockIdx.z, blockIdx.y, blockIdx.x * TY);
 }
 
@@ -221,7 +222,8 @@ __device__ __forceinline__ void zprod_column(float2* buf, int rs, int len, int n
     if (act) {
 #pragma unroll
       for (int zo = 0; zo < NZM; ++zo)
-        if (zo < nz) buf[(a * nz + zo) * rs + pidx<PADS>(k)] = out[zo];
+        if (zo < nz && MM_BC_SMEM(&buf[(a * nz + zo) * rs + pidx<PADS>(k)], sizeof(float2)))
+          buf[(a * nz + zo) * rs + pidx<PADS>(k)] = out[zo];
     }
     __syncwarp();
   }
@@ -302,7 +304,8 @@ __device__ __forceinline__ void zprod_column_chunked(float2* buf, int rs, int le
     if (act) {
 #pragma unroll
       for (int zo = 0; zo < 16; ++zo)
-        if (16 * c + zo < nz) buf[(a * nz + 16 * c + zo) * rs + pidx<PADS>(k)] = out[zo];
+        if (16 * c + zo < nz && MM_BC_SMEM(&buf[(a * nz + 16 * c + zo) * rs + pidx<PADS>(k)], sizeof(float2)))
+          buf[(a * nz + 16 * c + zo) * rs + pidx<PADS>(k)] = out[zo];
     }
     __syncwarp();
   }
@@ -421,7 +424,8 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
       const int p1 = min(NP, (g + 1) * rpg);
       mbar_arrive_expect_tx(&bar[g], (uint32_t)((p1 - g * rpg) * ny * sizeof(float2)));
       for (int p = g * rpg; p < p1; ++p)
-        bulk_g2s(buf + p * RS, Sk + (long long)p * ny, ny * sizeof(float2), &bar[g]);
+        if (MM_BC_SMEM(buf + p * RS, ny * sizeof(float2)) && MM_BC(kx < d.hx && p < NP))
+          bulk_g2s(buf + p * RS, Sk + (long long)p * ny, ny * sizeof(float2), &bar[g]);
     }
   };
   if (bulk && threadIdx.x == 0) {
@@ -470,7 +474,9 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
     if (bulk) {
       if (threadIdx.x == 0) issue_copies();
     } else {
-      for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) buf[(i / ny) * RS + i % ny] = ld_rw<PC>(Sk + i);
+      for (int i = threadIdx.x; i < NP * ny; i += blockDim.x)
+        if (MM_BC_SMEM(&buf[(i / ny) * RS + i % ny], sizeof(float2)) && MM_BC(kx < d.hx))
+          buf[(i / ny) * RS + i % ny] = ld_rw<PC>(Sk + i);
     }
   }
   // first y/z pass of a step: the last warp of CTA 0 advances the field
@@ -547,7 +553,7 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
       yz_rows_fft2<PY, 1>(buf, NP, PY, ny, twY, [](int) {}, [&](int p, bool act) {
         fence_proxy_async_smem();
         __syncwarp();
-        if (act && (threadIdx.x & 15) == 0) {
+        if (act && (threadIdx.x & 15) == 0 && MM_BC(kx < d.hx && p < NP)) {
           bulk_s2g(Sk + (long long)p * ny, buf + p * RS, ny * sizeof(float2));
           bulk_commit();
           issued = true;
@@ -559,7 +565,7 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
         if (PY > 1) team_fft_io<PY, T, 1, 1, PADS, PADS, 0>(buf + p * RS, t, mask, tws, PY, ny);
         fence_proxy_async_smem();
         __syncwarp(mask);
-        if (t == 0) {
+        if (t == 0 && MM_BC(kx < d.hx && p < NP)) {
           bulk_s2g(Sk + (long long)p * ny, buf + p * RS, ny * sizeof(float2));
           bulk_commit();
         }
@@ -580,18 +586,21 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   if (bulk) {
     if (threadIdx.x == 0) {
       fence_proxy_async_smem();
-      for (int p = 0; p < NP; ++p) bulk_s2g(Sk + (long long)p * ny, buf + p * RS, ny * sizeof(float2));
+      for (int p = 0; p < NP; ++p)
+        if (MM_BC(kx < d.hx)) bulk_s2g(Sk + (long long)p * ny, buf + p * RS, ny * sizeof(float2));
       bulk_commit();
       bulk_wait_read_all();
     }
   } else {
-    for (int i = threadIdx.x; i < NP * ny; i += blockDim.x) Sk[i] = buf[(i / ny) * RS + i % ny];
+    for (int i = threadIdx.x; i < NP * ny; i += blockDim.x)
+      if (MM_BC(kx < d.hx)) Sk[i] = buf[(i / ny) * RS + i % ny];
   }
 }
 
 template <int PY, int NZM, int PREC>
 __global__ void __launch_bounds__(512, 1) k_yz(float2* __restrict__ S, const float* __restrict__ Kh,
                                                 const float2* __restrict__ twY, Dims d, int* flag, Tick tk) {
+  MM_BC_ENTER(d.flag);
   body_yz<PY, NZM, PREC>(S, Kh, twY, d, flag, blockIdx.x, tk);
 }
 
@@ -615,6 +624,7 @@ __global__ void __launch_bounds__(256) k_yt(float2* __restrict__ S, float2* __re
   extern __shared__ __align__(16) float2 sm[];
   float2* tws = sm;
   float2* rows = sm + PY;
+  MM_BC_ENTER(d.flag);
   const int kx = blockIdx.x, ny = d.ny, NP = 3 * d.nz;
   const int nrows = blockDim.x / TM;
   const int r0 = blockIdx.y * nrows;
@@ -654,6 +664,7 @@ struct KyShift {
 template <int NZM>
 __global__ void __launch_bounds__(512, 1) k_zt(float2* __restrict__ T, const float* __restrict__ Kh, Dims d, int KB) {
   extern __shared__ __align__(16) float2 zb[];   // [3 nz][KB], then the tensor rows of the block
+  MM_BC_ENTER(d.flag);
   const int kx = blockIdx.x, ky0 = blockIdx.y * KB;
   const int nz = d.nz, NP = 3 * nz, py = d.py;
   const int len = py - ky0 < KB ? py - ky0 : KB;
@@ -745,6 +756,7 @@ __device__ __forceinline__ float3 cell_update(const StageArgs& a, const Phys& ph
                                               int x, int y, int z, float3 bd, float* kmag = nullptr) {
   const long long N = d.N;
   const long long cell = ((long long)z * d.ny + y) * d.nx + x;
+  if (!MM_BC(x < d.nx && y < d.ny && z < d.nz)) return make_float3(0.f, 0.f, 0.f);
   const float* __restrict__ mi = a.m_in;
   // eq. 5 with eq. 7: a missing neighbour is the cell itself (clamped index)
   const long long row = d.nx, pl = (long long)d.nx * d.ny;
@@ -881,6 +893,11 @@ __device__ __forceinline__ void cell_updateV(const StageArgs& a, const Phys& ph,
   using T = typename Vec::T;
   const long long N = d.N;
   const long long cell = ((long long)z * d.ny + y) * d.nx + x0;
+  if (!MM_BC(x0 + V <= d.nx && y < d.ny && z < d.nz)) {
+#pragma unroll
+    for (int j = 0; j < V; ++j) nm[j] = make_float3(0.f, 0.f, 0.f);
+    return;
+  }
   const long long row = d.nx, pl = (long long)d.nx * d.ny;
   const long long oym = y > 0 ? -row : 0, oyp = y < d.ny - 1 ? row : 0;
   const long long ozm = z > 0 ? -pl : 0, ozp = z < d.nz - 1 ? pl : 0;
@@ -1030,7 +1047,8 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
       const float2 w = tws[k];
       const float2 wm = make_float2(w.x, -w.y);
       const float2 Za = cadd(cadd(Xa, cconj(Xb)), cmuli(cmul(csub(Xa, cconj(Xb)), wm)));
-      if (k == 0 || k == k2) {
+      if (!MM_BC_SMEM(&row[pidx<PADS>(k2)], sizeof(float2)) || !MM_BC_SMEM(&row[pidx<PADS>(k)], sizeof(float2))) {
+      } else if (k == 0 || k == k2) {
         row[pidx<PADS>(k)] = Za;
       } else {
         const float2 wm2 = make_float2(-w.x, -w.y);
@@ -1236,7 +1254,8 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
       const int r = i % TY, rest = i / TY;
       const int c = rest % 3, k = rest / 3;
       const int y = y0 + r;
-      if (y < d.ny) S[(((long long)k * 3 + c) * d.nz + z) * d.ny + y] = rows[(c * TY + r) * RS + pidx<PADS>(k)];
+      if (y < d.ny && MM_BC(k < d.hx && z < d.nz))
+        S[(((long long)k * 3 + c) * d.nz + z) * d.ny + y] = rows[(c * TY + r) * RS + pidx<PADS>(k)];
     }
   }
 }
@@ -1251,6 +1270,7 @@ template <int HALF, bool DRIVE, int TYV, bool TMA>
 __global__ void __launch_bounds__(384, HALF >= 512 ? 1 : 2) k_x(StageArgs a, Phys ph, float2* __restrict__ S,
                                            const float2* __restrict__ twP, Dims d, int TY, int fwd,
                                            const __grid_constant__ CUtensorMap xmap) {
+  MM_BC_ENTER(d.flag);
   grid_dep_wait();     // S, the stage states and the drive slots: written by the kernels before
   grid_dep_launch();
   if constexpr (DRIVE) {
@@ -1499,6 +1519,7 @@ __global__ void __launch_bounds__(512) kb_xfwd(const BatchFilm* __restrict__ F, 
                                                int TY) {
   const int2 ft = map[blockIdx.x];
   const BatchFilm& f = F[ft.x];
+  MM_BC_ENTER(f.d.flag);
   if (!f.active) return;
   const int ntyl = (f.d.ny + TY - 1) / TY;
   const int c = ft.y / (f.d.nz * ntyl), rem = ft.y % (f.d.nz * ntyl);
@@ -1511,6 +1532,7 @@ __global__ void __launch_bounds__(512, 1) kb_yz(const BatchFilm* __restrict__ F,
                                                  int* flag) {
   const int2 ft = map[blockIdx.x];
   const BatchFilm& f = F[ft.x];
+  MM_BC_ENTER(f.d.flag);
   if (!f.active) return;
   body_yz<PY, NZM>(f.S, f.Kh, f.tw + PY, f.d, flag, ft.y);
 }
@@ -1520,6 +1542,7 @@ __global__ void __launch_bounds__(512) kb_x(const BatchFilm* __restrict__ F, con
                                             int stage, float dt) {
   const int2 ft = map[blockIdx.x];
   const BatchFilm& f = F[ft.x];
+  MM_BC_ENTER(f.d.flag);
   if (!f.active) return;
   const int ntyl = (f.d.ny + TY - 1) / TY;
   StageArgs a = {};

@@ -157,6 +157,7 @@ extern "C" int mm_heff_noalloc(const int grid[3], double delta, double Ms, doubl
   unsigned char* base = nullptr;
   if (int rc = mm_noalloc_scratch(&base)) return rc;
   int* flags = (int*)base;   // kernels' error flags, read by mm_noalloc_status
+  d.flag = flags;
   float* Kh = (float*)(base + fl_b);
   float2* tw = (float2*)(base + fl_b + kh_b);
   double2* Kc = (double2*)(base + fl_b + kh_b + tw_b);

@@ -13,11 +13,16 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmm_b300.so")
+# MM_B300_BOUNDS_CHECK=1 selects the bounds-check build of the library
+# (libmm_b300_bc.so: index checks in the kernels that report MM_EBOUNDS)
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                        "libmm_b300_bc.so" if os.environ.get("MM_B300_BOUNDS_CHECK") == "1" else "libmm_b300.so")
 
 MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ETIMEOUT, MM_ENONFINITE, MM_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+MM_EBOUNDS = -7
 STATUS_NAMES = {0: "MM_OK", -1: "MM_EINVAL", -2: "MM_ENOMEM", -3: "MM_ECUDA", -4: "MM_ETIMEOUT",
-                -5: "MM_ENONFINITE", -6: "MM_EUNSUPPORTED"}
+                -5: "MM_ENONFINITE", -6: "MM_EUNSUPPORTED",
+                -7: "MM_EBOUNDS"}
 MM_FP32, MM_SPLIT_BF16, MM_SPLIT_FP16 = 0, 1, 2
 MM_RK4, MM_EULER = 0, 1
 TERM_EXCHANGE, TERM_ANISOTROPY, TERM_DEMAG, TERM_ZEEMAN, TERM_ALL = 1, 2, 4, 8, 15
@@ -67,6 +72,7 @@ _SIGNATURES = {
     "mm_set_tuning": (_I, [_P, _I, _I]),
     "mm_get_tuning": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "mm_launch_count": (ctypes.c_longlong, [_P]),
+    "mm_build_flags": (_I, []),
     "mm_sync": (_I, [_P]),
     "mm_selftest_wait_timeout": (_I, [_P, ctypes.c_uint]),
     "mm_last_error": (ctypes.c_char_p, [_P]),

@@ -74,3 +74,16 @@ def test_create_without_gpu_fails_cleanly(libpath):
     rc = L.mm_create(ctypes.byref(ctx), g, d(4e-9), d(8e5), d(1.3e-11), d(0.0), d(0.02), d(1.76e11), None)
     assert rc != 0 and not ctx.value
     assert L.mm_last_error(None)
+
+
+def test_bounds_check_build_exports_the_same_boundary():
+    from paper_1501_07293_b300 import build
+    path = build.build(bounds_check=True)
+    L = ctypes.CDLL(path)
+    missing = [n for n in sorted(_declared()) if not hasattr(L, n)]
+    assert not missing, missing
+    L.mm_build_flags.restype = ctypes.c_int
+    assert L.mm_build_flags() & 1
+    L2 = ctypes.CDLL(build.build())
+    L2.mm_build_flags.restype = ctypes.c_int
+    assert L2.mm_build_flags() == 0
