@@ -45,6 +45,9 @@ def parse_args():
     ap.add_argument("--workload", default="film_256x256x16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-sweep and adjoint measurements")
+    ap.add_argument("--extras", default="all",
+                    help="comma list of the extra measurements to run: batched, adjoint, sp4, sp3, split, cufft, "
+                         "noalloc (default all)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16", "split_fp16"],
                     help="the z product of the timed steps: FP32 direct sum or the tensor-core split forms")
     ap.add_argument("--batch-max-steps", type=int, default=20000,
@@ -224,7 +227,7 @@ def stored_traffic(kernel):
         d = json.load(open(p))[kernel]
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_1501_07293_b300", "csrc", d.get("source", "field.cu"))
+    src = os.path.join(ROOT, "paper_1501_07293_b300", "csrc", d.get("source", "field_kernels.cuh"))
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
@@ -819,15 +822,24 @@ def b300_arm(args, w):
     nbytes = 3 * w.ncells * 4
 
     extra = {}
-    if not args.no_extras:
+    want = set() if args.no_extras else (
+        {"batched", "adjoint", "sp4", "sp3", "split", "cufft", "noalloc"} if args.extras == "all"
+        else set(args.extras.split(",")))
+    if "batched" in want:
         extra["batched"] = bench_batched(args)   # every rank: the films are sharded
-    if not args.no_extras and rank == 0:         # single-GPU measurements: rank 0 only
-        extra["adjoint"] = bench_adjoint(args)
-        extra["sp4_protocol"] = bench_sp4(args)
-        extra["sp3_table1"] = bench_sp3(args)
-        extra["split_precision"] = bench_split(args, 1e3 * t_max / K)
-        extra["cufft_comparison"] = bench_cufft(args, float(per_launch_ms["yz"] + per_launch_ms["x"]))
-        extra["noalloc"] = bench_noalloc(args)
+    if rank == 0:                                # single-GPU measurements: rank 0 only
+        if "adjoint" in want:
+            extra["adjoint"] = bench_adjoint(args)
+        if "sp4" in want:
+            extra["sp4_protocol"] = bench_sp4(args)
+        if "sp3" in want:
+            extra["sp3_table1"] = bench_sp3(args)
+        if "split" in want:
+            extra["split_precision"] = bench_split(args, 1e3 * t_max / K)
+        if "cufft" in want:
+            extra["cufft_comparison"] = bench_cufft(args, float(per_launch_ms["yz"] + per_launch_ms["x"]))
+        if "noalloc" in want:
+            extra["noalloc"] = bench_noalloc(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
