@@ -997,6 +997,85 @@ __device__ __forceinline__ float& rowf(float2* row, int x) {
   return (x & 1) ? e.y : e.x;
 }
 
+// The x transforms of a k_x tile at HALF = 256 with the TMA staging area
+// (TY = 8: 24 rows [c][r], 384 threads), as two register passes of 16
+// (256 = 16 x 16, fft.cuh reg_fft).  Thread t takes row rr = t % 24 and lane
+// l = t / 24: rows fastest, so the 24 rows' reads of one staged kx are
+// contiguous.  Pass 1 of lane l transforms the 16 values l + 16 j, multiplies
+// output k1 by W_256^(l k1) and stores it at k1 17 + l, which is pidx<4>(16 k1
+// + l) (the rows' padded layout); pass 2 of lane k1 transforms the 16 values
+// k1 17 + l and stores X[k1 + 16 k2] at pidx<4>(k1 + 16 k2).  tws is the
+// table exp(-2 pi i m / 512).
+static constexpr int kXFusedHalf = 256;
+
+template <int DIR>
+__device__ __forceinline__ void x16_pass2(float2* row, int k1, int nout) {
+  float2 u[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) u[q] = row[k1 * 17 + q];
+  __syncthreads();   // every thread has read its pass-2 inputs before any output lands
+  reg_fft<16, DIR>(u);
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) {
+    const int n = k1 + 16 * k2;
+    if (n < nout && MM_BC_SMEM(&row[pidx<4>(n)], sizeof(float2))) row[pidx<4>(n)] = u[brev(k2, 4)];
+  }
+}
+
+// Inverse, with the complex-to-real pre-processing in pass 1: Z[k] =
+// (X[k] + conj X[256-k]) + i W_512^-k (X[k] - conj X[256-k]) straight from the
+// staged spectrum (stg0: kx 0..128, stg1: kx 129..257, [kx][c][TY]).  Only the
+// first nout outputs are stored.
+template <int TY>
+__device__ __forceinline__ void x16_inverse_c2r(const float2* stg0, const float2* stg1, float2* rows, int RS,
+                                                const float2* tws, int nout) {
+  constexpr int H = kXFusedHalf, XB = 129, NR = 3 * TY;
+  const int rr = threadIdx.x % NR, l = threadIdx.x / NR;
+  const int c = rr / TY, r = rr % TY;
+  float2* row = rows + rr * RS;
+  auto stg = [&](int k) { return k < XB ? stg0[(k * 3 + c) * TY + r] : stg1[((k - XB) * 3 + c) * TY + r]; };
+  float2 v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int k = l + 16 * j;
+    const float2 Xa = stg(k), Xb = cconj(stg(H - k));
+    v[j] = cadd(cadd(Xa, Xb), cmuli(cmul(csub(Xa, Xb), cconj(tws[k]))));
+  }
+  reg_fft<16, 1>(v);
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) {
+    const float2 x = v[brev(k1, 4)];
+    if (MM_BC_SMEM(&row[k1 * 17 + l], sizeof(float2))) row[k1 * 17 + l] = k1 ? cmul(x, cconj(tws[2 * ((l * k1) & (H - 1))])) : x;
+  }
+  __syncthreads();
+  x16_pass2<1>(row, l, nout);
+}
+
+// Forward of the rows whose y is inside the film; only the first nin inputs
+// are read (the rest are zeros: the upper half of every pass-1 sequence).
+template <int TY>
+__device__ __forceinline__ void x16_forward(float2* rows, int RS, const float2* tws, int nin, bool act) {
+  constexpr int H = kXFusedHalf, NR = 3 * TY;
+  const int rr = threadIdx.x % NR, l = threadIdx.x / NR;
+  float2* row = rows + rr * RS;
+  float2 v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int n = l + 16 * j;
+    v[j] = (j < 8 && act && n < nin) ? row[pidx<4>(n)] : make_float2(0.f, 0.f);
+  }
+  reg_fft<16, -1, true>(v);
+  if (act) {   // in place: thread (l, rr) overwrites only the slots it has read
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) {
+      const float2 x = v[brev(k1, 4)];
+      if (MM_BC_SMEM(&row[k1 * 17 + l], sizeof(float2))) row[k1 * 17 + l] = k1 ? cmul(x, tws[2 * ((l * k1) & (H - 1))]) : x;
+    }
+  }
+  __syncthreads();
+  x16_pass2<-1>(row, l, act ? H : 0);
+}
+
 // TMA: the S tile arrives as two tiled tensor copies (kx 0..128 and 129..257)
 // into a staging area [kx][c][TY] (xmap: the tensor map of S), instead of
 // per-thread copies; the C2R pre-processing then reads the staging area.
@@ -1085,7 +1164,9 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
         mbar_wait_bounded(&xbar, 0);
         return;
       }
-      // rows fastest: the staging reads are contiguous across lanes
+      // rows fastest: the staging reads are contiguous across lanes (at HALF =
+      // 256 the inverse transform's first pass reads the staging area itself)
+      if constexpr (HALF != kXFusedHalf)
       for (int i = threadIdx.x; i < NR * npair; i += blockDim.x) {
         const int r = i % TY, c = (i / TY) % 3, k = i / (3 * TY), kb = HALF - k;
         const float2 Xa = k < XB ? stg0[(k * 3 + c) * TY + r] : stg1[((k - XB) * 3 + c) * TY + r];
@@ -1117,7 +1198,17 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
     const int lane = threadIdx.x & 31;
     const int team = threadIdx.x / T, t = threadIdx.x % T, nteams = blockDim.x / T;
     const unsigned mask = team_mask<T>(lane);
-    for (int rr = team; rr < NR; rr += nteams) team_fft<HALF, T, 1, 2, PADS>(rows + rr * RS, t, mask, tws);
+    if constexpr (TMA && HALF == kXFusedHalf) {
+      static_assert(TY == 8, "24 rows x 16 lanes = 384 threads");
+      constexpr uint32_t box_bytes = 129 * 3 * TY * sizeof(float2);
+      float2* rend = rows + 3 * TY * RS;
+      const uint32_t s0 = (smem_u32(rend) + 127u) & ~127u;
+      const uint32_t s1 = (s0 + box_bytes + 127u) & ~127u;
+      float2* stg0 = rend + (s0 - smem_u32(rend)) / sizeof(float2);
+      x16_inverse_c2r<TY>(stg0, stg0 + (s1 - s0) / sizeof(float2), rows, RS, tws, (d.nx + 1) / 2);
+    } else {
+      for (int rr = team; rr < NR; rr += nteams) team_fft<HALF, T, 1, 2, PADS>(rows + rr * RS, t, mask, tws);
+    }
     __syncthreads();
     float kmax = 0.f;
     if ((a.mode == 1 || a.mode == 2) && (d.nx % XV) == 0) {
@@ -1178,9 +1269,13 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
     }
     __syncthreads();
     const int nin = (d.nx + 1) / 2;
-    for (int rr = team; rr < NR; rr += nteams) {
-      if (y0 + rr % TY >= d.ny) continue;
-      team_fft_io<HALF, T, -1, 2, PADS, PADS, PADS>(rows + rr * RS, t, mask, tws, nin, HALF);
+    if constexpr (TMA && HALF == kXFusedHalf) {
+      x16_forward<TY>(rows, RS, tws, nin, y0 + (int)(threadIdx.x % NR) % TY < d.ny);
+    } else {
+      for (int rr = team; rr < NR; rr += nteams) {
+        if (y0 + rr % TY >= d.ny) continue;
+        team_fft_io<HALF, T, -1, 2, PADS, PADS, PADS>(rows + rr * RS, t, mask, tws, nin, HALF);
+      }
     }
     __syncthreads();
     // X[k] = 1/2 (Z[k] + conj Z[-k]) - i/2 W_P^k (Z[k] - conj Z[-k]), by pairs (k, HALF-k)
