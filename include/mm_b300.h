@@ -63,8 +63,8 @@ enum {
 };
 
 typedef struct {
-  int precision;    /* MM_FP32 (default): the demag product along z as an FP32 direct
-                       sum.  MM_SPLIT_BF16 / MM_SPLIT_FP16: that product through a
+  int precision;    /* MM_FP32 (default): the demag product along z in FP32 (see zform).
+                       MM_SPLIT_BF16 / MM_SPLIT_FP16: that product through a
                        length-2nz DFT along z computed as GEMMs on the tensor cores
                        (tcgen05) with 16-bit hi+lo split operands (x = hi + lo,
                        products hi*hi + hi*lo + lo*hi, FP32 accumulation; FP16 with
@@ -87,10 +87,22 @@ typedef struct {
                        applies the y/z route and ky block recorded for this grid's
                        padded size and precision, as mm_set_tuning would.  NULL, a
                        missing file or a missing entry keep the built-in choice.     */
+  int zform;        /* MM_FP32 only: how the demag product of eq. 14 runs along z.
+                       MM_ZFORM_AUTO (default): as a length-32 circular convolution
+                       through register transforms along z against the tensor
+                       transformed along z as well (one extra FP32 array of
+                       17 x 6 x hx x hy values, built by mm_create), wherever the
+                       fused y/z kernel takes the film (9..16 planes, padded y of 256
+                       or 512); elsewhere, and with MM_ZFORM_DIRECT, as the direct
+                       Toeplitz sum over the nz planes against the tensor transformed
+                       along x and y only.  Both are exact (eq. 13 restricted to z);
+                       they differ by FP32 rounding only.                            */
 } mm_opts;
 
+enum { MM_ZFORM_AUTO = 0, MM_ZFORM_DIRECT = 1 };   /* mm_opts.zform */
+
 /* Fill *opts with the defaults: MM_FP32, MM_RK4, self_term 1, obs_every 0, NULL stream,
- * no tune cache. */
+ * no tune cache, MM_ZFORM_AUTO. */
 void mm_default_opts(mm_opts* opts);
 
 /*

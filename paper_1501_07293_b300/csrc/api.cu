@@ -106,6 +106,7 @@ extern "C" void mm_default_opts(mm_opts* o) {
   o->obs_every = 0;
   o->stream = nullptr;
   o->tune_cache = nullptr;
+  o->zform = MM_ZFORM_AUTO;
 }
 
 static void free_ctx(mm_ctx* c) {
@@ -188,6 +189,8 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double M
   if (o.integrator != MM_RK4 && o.integrator != MM_EULER)
     return mm_fail(nullptr, MM_EINVAL, "unknown integrator %d", o.integrator);
   if (o.obs_every < 0) return mm_fail(nullptr, MM_EINVAL, "obs_every = %d < 0", o.obs_every);
+  if (o.zform != MM_ZFORM_AUTO && o.zform != MM_ZFORM_DIRECT)
+    return mm_fail(nullptr, MM_EINVAL, "unknown zform %d", o.zform);
 
   int rc = MM_OK;
   mm_ctx* c = (mm_ctx*)calloc(1, sizeof(mm_ctx));
@@ -264,6 +267,10 @@ extern "C" int mm_create(mm_ctx** out, const int grid[3], double delta, double M
   }
   rc = mm_build_kernel(c);
   if (rc == MM_OK && c->d.prec != MM_FP32) rc = mm_build_split(c);
+  // the transform form of the z product: 9..16 planes, py = 256 / 512, fused y/z kernel
+  if (rc == MM_OK && c->d.prec == MM_FP32 && o.zform == MM_ZFORM_AUTO && mm_nzm(c->d.nz) == 16 &&
+      (c->d.py == 256 || c->d.py == 512) && mm_yz_fused(c->d))
+    rc = mm_build_kz(c);
   if (rc != MM_OK) {
     snprintf(g_create_err, sizeof g_create_err, "%s", c->err);
     goto fail;

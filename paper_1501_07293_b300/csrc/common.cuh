@@ -73,6 +73,8 @@ struct Dims {
   int route;                   // y/z pass: 0 built-in choice, 1 fused kernel, 2 split pass (mm_set_tuning)
   int ztkb;                    // split pass: ky block of the z product (0: built-in choice)
   int pdl;                     // stage kernels launched with programmatic serialization (large grids)
+  int zfft;                    // FP32 fused y/z pass: the z product as a length-32 transform against Kt
+                               // (9..16 planes, py = 256 or 512); 0: the direct sum against Kh
   int* flag;                   // the context's device error flags (bounds-check builds report to [2])
 };
 
@@ -288,6 +290,7 @@ int mm_fail(mm_ctx* c, int code, const char* fmt, ...);
 int mm_build_kernel(mm_ctx* c);
 // setup.cu: the split-precision operands Kt and Bdft (allocated and built; d.Kt, d.Bdft set)
 int mm_build_split(mm_ctx* c);
+int mm_build_kz(mm_ctx* c);
 // field.cu: padded z size (power of two >= nz) the z product works with
 int mm_nzm(int nz);
 // field.cu: 1 if one CTA holds a kx column (the fused y/z kernel), 0 if the

@@ -315,6 +315,116 @@ struct KyIdentity {
   __device__ int operator()(int k) const { return k; }
 };
 
+// Column buffer of the y/z pass: 3 nz rows of stride RS (padded for the
+// Stockham passes, natural order for the two-pass transform).
+template <int PY>
+struct YzLayout {
+  static constexpr int PADS = PY >= 32 ? 4 : 0;
+  static constexpr int RS = PY + (PADS ? PY / 16 : 0) + 2;   // even: rows stay 16-byte aligned
+};
+
+// ---------------------------------------------------------------------------
+// The product of eq. 14 along z as a transform (films of 9..16 planes, py = 256
+// or 512, natural ky order in the column buffer).  For nz <= 16 the linear
+// convolution along z equals a circular one of length 32:
+//   out_a(z) = sum_kz e^{+2 pi i kz z / 32} sum_b Kz_ab(kz) X_b(kz),
+//   X_b(kz)  = sum_{z < nz} m_b(z) e^{-2 pi i kz z / 32},
+// with Kz the tensor transformed along z (Kt: real for every pair, the 1/32 of
+// the inverse folded in; pairs odd in z change sign at kz > 16, pairs odd in y
+// at a mirrored ky).  The 32 frequencies split into two halves of 16:
+//   X_b(2k)     = DFT16[m_b(z)](k),   X_b(2k + 1) = DFT16[m_b(z) W32^z](k),
+//   out_a(z)    = IDFT16[Y_a(2k)](z) + W32^-z IDFT16[Y_a(2k + 1)](z).
+// Two lanes share a position ky: lane half h (0: even, 1: odd frequencies)
+// holds all three components of its half in registers (16-point register
+// transforms, fft.cuh reg_fft), applies the 3 x 3 product per kz, and
+// transforms back.  The odd lane keeps its sequence rotated by 8 planes
+// (register r holds plane (r + 8) mod 16), which multiplies its spectrum by
+// (-1)^k and rotates its inverse output back by 8; then both lanes exchange
+// registers 8..15 and keep 0..7, so the even lane ends with out(0..7) and the
+// odd lane with out(8..15), with no selects.  A warp takes 16 positions; every
+// lane reads its inputs before any lane of the warp writes (__syncwarp).
+// ---------------------------------------------------------------------------
+template <int PY>
+__device__ __forceinline__ void zprod_fft_column(float2* buf, int nz, const float* __restrict__ Kt_col) {
+  constexpr int RS = YzLayout<PY>::RS;
+  constexpr int HY = PY / 2 + 1;
+  static_assert(PY == 256 || PY == 512, "natural-order columns of 256 or 512");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int h = lane >> 4, j = lane & 15;
+  const int h8 = h << 3;
+  for (int g = warp; g < PY / 16; g += nwarps) {
+    const int ky = 16 * g + j;
+    const bool mirrored = ky > PY / 2;
+    const int kyf = mirrored ? PY - ky : ky;
+    const float ys = mirrored ? -1.f : 1.f;
+    float2 v[3][16];
+    // forward: even lane v[r] = m(r); odd lane v[r] = m(zt) W32^zt, zt = (r + 8) mod 16
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      // plane zt = r + h8 (r < 8) or r - h8 (r >= 8): compile-time offsets from two bases
+      const float2* lo = buf + (b * nz + h8) * RS + ky;
+      const float2* hi = buf + (b * nz - h8) * RS + ky;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int zt = r < 8 ? r + h8 : r - h8;
+        v[b][r] = zt < nz ? (r < 8 ? lo : hi)[r * RS] : make_float2(0.f, 0.f);
+      }
+      if (h) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[b][r] = mul_w32<-1>(v[b][r], (r + 8) & 15);
+      }
+      reg_fft<16, -1>(v[b]);   // spectrum index k at v[b][brev(k)]
+    }
+    // 3 x 3 product per frequency kz = 2k + h; Kt holds kz <= 16, kz > 16 reads 32 - kz
+    const float* kp = Kt_col + kyf + h * 6 * HY;   // kz = 2k + h   (k <= 7)
+    const float* km = Kt_col + kyf - h * 6 * HY;   // kz = 32 - 2k - h (k >= 8)
+    const float s8 = h ? -1.f : 1.f;               // z parity at k = 8 (kz 16 or 17)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float* kb = k <= 7 ? kp + (2 * k) * 6 * HY : km + (32 - 2 * k) * 6 * HY;
+      const float zs = k <= 7 ? 1.f : (k == 8 ? s8 : -1.f);
+      const float kxx = __ldg(kb + 0 * HY), kyy = __ldg(kb + 1 * HY), kzz = __ldg(kb + 2 * HY);
+      const float kxy = ys * __ldg(kb + 3 * HY);
+      const float kxz = zs * __ldg(kb + 4 * HY);
+      const float kyz = (ys * zs) * __ldg(kb + 5 * HY);
+      const int q = brev(k, 4);
+      const float2 x0 = v[0][q], x1 = v[1][q], x2 = v[2][q];
+      v[0][q] = __ffma2_rn(make_float2(kxz, kxz), x2, __ffma2_rn(make_float2(kxy, kxy), x1, __fmul2_rn(make_float2(kxx, kxx), x0)));
+      v[1][q] = __ffma2_rn(make_float2(kyz, kyz), x2, __ffma2_rn(make_float2(kyy, kyy), x1, __fmul2_rn(make_float2(kxy, kxy), x0)));
+      v[2][q] = __ffma2_rn(make_float2(kzz, kzz), x2, __ffma2_rn(make_float2(kyz, kyz), x1, __fmul2_rn(make_float2(kxz, kxz), x0)));
+    }
+    // inverse: natural frequency order by renaming, then register r holds the
+    // half's contribution at plane r (even) or (r + 8) mod 16 (odd, after W32^-z)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float2 w[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) w[k] = v[a][brev(k, 4)];
+      reg_fft<16, 1>(w);   // plane r at w[brev(r)]
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[a][r] = w[brev(r, 4)];
+      if (h) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[a][r] = mul_w32<1>(v[a][r], (r + 8) & 15);
+      }
+    }
+    __syncwarp();   // every lane of the warp has read its inputs
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float2* col = buf + a * nz * RS + ky;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float2 o;
+        o.x = __shfl_xor_sync(0xffffffffu, v[a][8 + i].x, 16);
+        o.y = __shfl_xor_sync(0xffffffffu, v[a][8 + i].y, 16);
+        const int z = h8 + i;
+        if (z < nz && MM_BC_SMEM(&col[z * RS], sizeof(float2))) col[z * RS] = cadd(v[a][i], o);
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // k_yz: CTA = one kx column, all 3 components and nz planes in shared memory.
 //  1. the column's 3 nz rows of ny values arrive by bulk copies (TMA engine)
@@ -333,12 +443,6 @@ struct KyIdentity {
 // A failed bounded wait sets flag[1] and abandons the column.
 // ---------------------------------------------------------------------------
 static constexpr int YZ_GROUPS = 8;   // copy groups (mbarriers) of a y/z column on large grids
-
-template <int PY>
-struct YzLayout {
-  static constexpr int PADS = PY >= 32 ? 4 : 0;
-  static constexpr int RS = PY + (PADS ? PY / 16 : 0) + 2;   // even: rows stay 16-byte aligned
-};
 
 // The y transforms of the 3 nz rows of a column by the two-pass transform of
 // fft.cuh (py = 256, 512).  Warp w owns rows p = w + nwarps i; pass 1 takes them
@@ -401,6 +505,9 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   // transforms); other sizes: the Stockham passes (padded order in between)
   constexpr bool FFT2 = (PY == 256 || PY == 512);
   constexpr int ZPADS = FFT2 ? 0 : PADS;   // layout the z product reads
+  // the z product as a length-32 transform (zprod_fft_column) when the context
+  // built Kt for it (d.zfft); the batch kernel (PC) keeps the direct sum
+  constexpr bool ZFFT_OK = FFT2 && NZM == 16 && PREC == 0 && !PC;
   extern __shared__ __align__(16) float2 sm[];
   float2* tws = sm;        // exp(-2 pi i m / PY), m < PY
   float2* buf = sm + PY;   // [3 nz][RS]
@@ -461,9 +568,10 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   {
     // the column's slice of the transformed tensor is first read by the z
     // product, after the transforms: start bringing it into L2 now
-    const char* kc = PREC ? reinterpret_cast<const char*>(d.Kt + (long long)kx * d.hy * (NZM + 1) * 6)
-                          : reinterpret_cast<const char*>(Kh + (long long)kx * d.hy * 6 * nz);
-    const int bytes = PREC ? d.hy * (NZM + 1) * 6 * (int)sizeof(float) : d.hy * 6 * nz * (int)sizeof(float);
+    const bool kz = PREC || ZFFT_OK && d.zfft;   // the z-transformed tensor Kt
+    const char* kc = kz ? reinterpret_cast<const char*>(d.Kt + (long long)kx * d.hy * (NZM + 1) * 6)
+                        : reinterpret_cast<const char*>(Kh + (long long)kx * d.hy * 6 * nz);
+    const int bytes = kz ? d.hy * (NZM + 1) * 6 * (int)sizeof(float) : d.hy * 6 * nz * (int)sizeof(float);
     const int nlines = (bytes + 127) >> 7;
     for (int i = threadIdx.x; i < nlines; i += blockDim.x) prefetch_l2(kc + ((long long)i << 7));
   }
@@ -540,7 +648,9 @@ __device__ __forceinline__ void body_yz(float2* __restrict__ S, const float* __r
   } else if constexpr (NZM > 16)
     zprod_column_chunked<NZM, (PY > 1 ? ZPADS : 0)>(buf, RS, PY, nz, Kh + (long long)kx * d.hy * 6 * nz, PY,
                                                     KyIdentity());
-  else if (PY > 1)
+  else if (ZFFT_OK && d.zfft) {
+    if constexpr (ZFFT_OK) zprod_fft_column<PY>(buf, nz, d.Kt + (long long)kx * d.hy * (NZM + 1) * 6);
+  } else if (PY > 1)
     zprod_column<NZM, ZPADS>(buf, RS, PY, nz, Kh + (long long)kx * d.hy * 6 * nz, d.hy, PY, KyIdentity());
   else
     zprod_column<NZM, 0>(buf, RS, PY, nz, Kh + (long long)kx * 6 * nz * d.hy, d.hy, PY, KyIdentity());

@@ -368,14 +368,36 @@ static void split16(double v, int prec, uint16_t* hi, uint16_t* lo) {
 // no-swizzle K-major layout (core matrices of 8 rows x 16 bytes)
 static size_t canon(int n, int k, int N) { return ((size_t)(k / 8) * (N / 8) + n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2; }
 
+// Kt from Kh (above), PZ = 2 * NZM; synchronises the context's stream.
+static int build_kt(mm_ctx* c) {
+  Dims& d = c->d;
+  const int PZ = 2 * mm_nzm(d.nz);
+  const long long nkt = (long long)d.hx * d.hy * (PZ / 2 + 1) * 6;
+  if (!c->Kt && cudaMalloc(&c->Kt, sizeof(float) * nkt) != cudaSuccess) {
+    cudaGetLastError();
+    c->Kt = nullptr;
+    return mm_fail(c, MM_ENOMEM, "cannot allocate the z-transformed tensor");
+  }
+  const long long tot = (long long)d.hx * d.hy * (PZ / 2 + 1);
+  k_ktz<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(c->Kh, c->Kt, d, PZ);
+  MM_CK(c, cudaGetLastError());
+  c->launches++;
+  MM_CK(c, cudaStreamSynchronize(c->stream));
+  d.Kt = c->Kt;
+  return MM_OK;
+}
+
+// FP32 path: the z product as a length-32 transform (field_kernels.cuh
+// zprod_fft_column) needs Kt with PZ = 32.
+int mm_build_kz(mm_ctx* c) {
+  const int rc = build_kt(c);
+  if (rc == MM_OK) c->d.zfft = 1;
+  return rc;
+}
+
 int mm_build_split(mm_ctx* c) {
   Dims& d = c->d;
   const int NZ = mm_nzm(d.nz), PZ = 2 * NZ;
-  const long long nkt = (long long)d.hx * d.hy * (PZ / 2 + 1) * 6;
-  if (cudaMalloc(&c->Kt, sizeof(float) * nkt) != cudaSuccess) {
-    cudaGetLastError();
-    return mm_fail(c, MM_ENOMEM, "split precision: cannot allocate the z-transformed tensor");
-  }
   // GEMM 1 operand B1 (2 PZ x 2 NZ): rows re kz | im kz, columns re z | im z of
   //   sum_z m(z) e^{-2 pi i kz z / PZ}:  re = sum re cos + im sin,  im = sum im cos - re sin
   // GEMM 2 operand B2 (2 NZ x 2 PZ): rows re z | im z, columns re kz | im kz of
@@ -410,12 +432,6 @@ int mm_build_split(mm_ctx* c) {
     return mm_fail(c, MM_ENOMEM, "split precision: cannot allocate the DFT operands");
   }
   MM_CK(c, cudaMemcpy(c->Bdft, h.data(), h.size(), cudaMemcpyHostToDevice));
-  const long long tot = (long long)d.hx * d.hy * (PZ / 2 + 1);
-  k_ktz<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(c->Kh, c->Kt, d, PZ);
-  MM_CK(c, cudaGetLastError());
-  c->launches++;
-  MM_CK(c, cudaStreamSynchronize(c->stream));
-  d.Kt = c->Kt;
   d.Bdft = c->Bdft;
-  return MM_OK;
+  return build_kt(c);
 }

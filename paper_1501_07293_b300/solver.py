@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "MM_OK", -1: "MM_EINVAL", -2: "MM_ENOMEM", -3: "MM_ECUDA", -4
                 -7: "MM_EBOUNDS"}
 MM_FP32, MM_SPLIT_BF16, MM_SPLIT_FP16 = 0, 1, 2
 MM_RK4, MM_EULER = 0, 1
+MM_ZFORM_AUTO, MM_ZFORM_DIRECT = 0, 1
 TERM_EXCHANGE, TERM_ANISOTROPY, TERM_DEMAG, TERM_ZEEMAN, TERM_ALL = 1, 2, 4, 8, 15
 
 
@@ -36,7 +37,8 @@ class MMError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("integrator", ctypes.c_int), ("self_term", ctypes.c_int),
-                ("obs_every", ctypes.c_int), ("stream", ctypes.c_void_p), ("tune_cache", ctypes.c_char_p)]
+                ("obs_every", ctypes.c_int), ("stream", ctypes.c_void_p), ("tune_cache", ctypes.c_char_p),
+                ("zform", ctypes.c_int)]
 
 
 class Segment(ctypes.Structure):
@@ -131,7 +133,8 @@ class Solver:
 
     def __init__(self, grid: Sequence[int], delta: float, Ms: float, A: float, Ku: float, alpha: float,
                  gamma: float, integrator: str = "rk4", self_term: bool = True, device=None, stream=None,
-                 precision: str = "fp32", obs_every: int = 0, tune_cache: Optional[str] = None):
+                 precision: str = "fp32", obs_every: int = 0, tune_cache: Optional[str] = None,
+                 zform: str = "auto"):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
@@ -147,6 +150,7 @@ class Solver:
         o.obs_every = int(obs_every)
         # launch shapes an earlier autotune stored for this size (applied by mm_create)
         o.tune_cache = None if tune_cache is None else os.fsencode(tune_cache)
+        o.zform = {"auto": MM_ZFORM_AUTO, "direct": MM_ZFORM_DIRECT}[zform]
         with torch.cuda.device(self.device):
             s = torch.cuda.current_stream() if stream is None else stream
             o.stream = s.cuda_stream

@@ -24,15 +24,17 @@ GRIDS = [(40, 10, 1), (7, 5, 3), (1, 1, 1), (2, 1, 1), (1, 9, 1), (1, 1, 7), (9,
          # thick samples: the chunked z product (17..32 and 33..64 planes), ragged chunks
          (8, 8, 17), (5, 3, 33), (20, 9, 24), (1, 1, 40), (3, 1, 64), (24, 20, 64),
          # columns beyond one CTA: the split y/z pass (y transforms and z product through a buffer)
-         (20, 200, 40), (6, 5, 100), (9, 70, 65), (1, 40, 128)]
+         (20, 200, 40), (6, 5, 100), (9, 70, 65), (1, 40, 128),
+         # the z product as a length-32 transform along z (9..16 planes, padded y of 256 / 512)
+         (9, 100, 11), (6, 130, 16), (12, 70, 9), (3, 256, 16), (5, 129, 13)]
 
 
 def _compare(grid, delta=4e-9, Ku=5e4, b_ext=(0.01, -0.02, 0.005), seed=7, self_term=True,
-             hmap=False, kumap=False):
+             hmap=False, kumap=False, zform="auto"):
     m = inputs.random_state(grid, seed)
     hm = inputs.zeeman_map(grid, seed + 1) if hmap else None
     km = inputs.ku_map(grid, seed + 2) if kumap else None
-    s = make_solver(grid, delta, Ku=Ku, self_term=self_term)
+    s = make_solver(grid, delta, Ku=Ku, self_term=self_term, zform=zform)
     import torch
     s.set_field(b_ext, None if hm is None else torch.from_numpy(hm).cuda(),
                 None if km is None else torch.from_numpy(km).cuda())
@@ -54,7 +56,15 @@ def test_heff_matches_oracle(grid):
         assert e <= TOL, (grid, t, e)
 
 
-@pytest.mark.parametrize("grid", [(40, 10, 1), (12, 7, 3)])
+@pytest.mark.parametrize("grid", [(9, 100, 11), (6, 130, 16)])
+def test_heff_direct_z_sum_matches_oracle(grid):
+    # the same grids with the z product forced to the direct Toeplitz sum
+    err = _compare(grid, zform="direct")
+    for t, e in err.items():
+        assert e <= TOL, (grid, t, e)
+
+
+@pytest.mark.parametrize("grid", [(40, 10, 1), (12, 7, 3), (6, 130, 16)])
 def test_heff_with_maps(grid):
     err = _compare(grid, hmap=True, kumap=True)
     for t, e in err.items():
@@ -78,10 +88,11 @@ def test_demag_direct_sum_route():
     assert rel_l2(Hg, Ho) <= TOL
 
 
-def test_heff_full_size_256x256x16():
+@pytest.mark.parametrize("zform", ["auto", "direct"])
+def test_heff_full_size_256x256x16(zform):
     w = inputs.film_256x256x16()
     m = inputs.workload_state(w)
-    s = make_solver(w.grid, w.delta, Ms=w.mat.Ms, A=w.mat.A, Ku=w.mat.Ku, alpha=w.mat.alpha)
+    s = make_solver(w.grid, w.delta, Ms=w.mat.Ms, A=w.mat.A, Ku=w.mat.Ku, alpha=w.mat.alpha, zform=zform)
     s.set_field(w.b_ext)
     film = make_film(w.grid, w.delta, Ms=w.mat.Ms, A=w.mat.A, Ku=w.mat.Ku, b_ext=w.b_ext)
     mo = to_xyz(m)
