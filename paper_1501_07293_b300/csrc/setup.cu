@@ -327,25 +327,30 @@ extern "C" int mm_tensor_eval(const int* offsets, int n, double* out) {
 // FP64 arithmetic on the FP32 Kh values.
 // ---------------------------------------------------------------------------
 __global__ void k_ktz(const float* __restrict__ Kh, float* __restrict__ Kt, Dims d, int PZ) {
+  // one thread per (kx, ky); cos / sin (2 pi kz dz / PZ) tabulated once per block
+  // (kz <= PZ / 2, dz < nz <= PZ / 2) instead of one sincospi per term
+  __shared__ double cs[33 * 32], sn[33 * 32];
   const int nkz = PZ / 2 + 1;
-  const long long total = (long long)d.hx * d.hy * nkz;
+  for (int i = threadIdx.x; i < nkz * d.nz; i += blockDim.x) {
+    const int kz = i / d.nz, dz = i % d.nz;
+    sincospi(2.0 * ((kz * dz) % PZ) / PZ, &sn[i], &cs[i]);
+  }
+  __syncthreads();
+  const long long total = (long long)d.hx * d.hy;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   const int ky = (int)(idx % d.hy);
-  const int kz = (int)((idx / d.hy) % nkz);
-  const int kx = (int)(idx / ((long long)d.hy * nkz));
-  const long long col = (long long)kx * d.hy + ky;
+  const int kx = (int)(idx / d.hy);
   for (int p = 0; p < 6; ++p) {
-    const float* k = Kh + (col * 6 + p) * d.nz;
-    double s;
-    if (p < 4) {
-      s = k[0];
-      for (int dz = 1; dz < d.nz; ++dz) s += 2.0 * k[dz] * cospi(2.0 * kz * dz / PZ);
-    } else {
-      s = 0.0;
-      for (int dz = 1; dz < d.nz; ++dz) s += 2.0 * k[dz] * sinpi(2.0 * kz * dz / PZ);
+    const float* k = Kh + (idx * 6 + p) * d.nz;
+    float kv[32];
+    for (int dz = 0; dz < d.nz; ++dz) kv[dz] = k[dz];
+    for (int kz = 0; kz < nkz; ++kz) {
+      const double* t = (p < 4 ? cs : sn) + kz * d.nz;
+      double s = p < 4 ? (double)kv[0] : 0.0;
+      for (int dz = 1; dz < d.nz; ++dz) s += 2.0 * (double)kv[dz] * t[dz];
+      Kt[(((long long)kx * nkz + kz) * 6 + p) * d.hy + ky] = (float)(s / PZ);
     }
-    Kt[(((long long)kx * nkz + kz) * 6 + p) * d.hy + ky] = (float)(s / PZ);
   }
 }
 
@@ -378,7 +383,7 @@ static int build_kt(mm_ctx* c) {
     c->Kt = nullptr;
     return mm_fail(c, MM_ENOMEM, "cannot allocate the z-transformed tensor");
   }
-  const long long tot = (long long)d.hx * d.hy * (PZ / 2 + 1);
+  const long long tot = (long long)d.hx * d.hy;
   k_ktz<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(c->Kh, c->Kt, d, PZ);
   MM_CK(c, cudaGetLastError());
   c->launches++;

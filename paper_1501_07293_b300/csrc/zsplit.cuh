@@ -232,6 +232,21 @@ __device__ __forceinline__ bool zprod_split(float2* buf, int rs, int nz, int py,
       }
       mma_commit(bar);
     }
+    // the tensor values of this thread's ky and kz range (step 3) do not depend on
+    // GEMM 1: their loads go out before its completion wait and land under it; Kt is
+    // [kz][pair][ky] per column, so a warp's loads are contiguous
+    const int kz0 = KW * g;
+    const bool mir = ky > py / 2;
+    const int kyf = mir ? py - ky : ky;
+    float2 kv[KW][3];
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+      const int kz = kz0 + j;
+      const int kzf = kz > PZ / 2 ? PZ - kz : kz;
+      const float* kp = Kt + (long long)kzf * 6 * hy + kyf;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) kv[j][u] = make_float2(__ldg(kp + (2 * u) * hy), __ldg(kp + (2 * u + 1) * hy));
+    }
     if (!wait_phase(bar, phase)) {
       if (tid == 0) atomicOr(flag + 1, 1);
       return false;
@@ -240,20 +255,6 @@ __device__ __forceinline__ bool zprod_split(float2* buf, int rs, int nz, int py,
     fence_after();
     // 3. H^_a(kz) for this thread's ky and kz in [KW g, KW g + KW)
     {
-      const int kz0 = KW * g;
-      const bool mir = ky > py / 2;
-      const int kyf = mir ? py - ky : ky;
-      // the tensor values of this thread's kz range first (their loads overlap the
-      // tensor-memory reads); Kt is [kz][pair][ky] per column, so a warp's loads are contiguous
-      float2 kv[KW][3];
-#pragma unroll
-      for (int j = 0; j < KW; ++j) {
-        const int kz = kz0 + j;
-        const int kzf = kz > PZ / 2 ? PZ - kz : kz;
-        const float* kp = Kt + (long long)kzf * 6 * hy + kyf;
-#pragma unroll
-        for (int u = 0; u < 3; ++u) kv[j][u] = make_float2(__ldg(kp + (2 * u) * hy), __ldg(kp + (2 * u + 1) * hy));
-      }
       float re[3][KW], im[3][KW];
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
