@@ -21,13 +21,15 @@
 // the two core matrices along K) and SBO = 128 (between 8-row groups).
 //
 // The ky positions are processed in chunks of 128 (one MMA M tile per lane
-// block of tensor memory).  Per chunk: threads write A1 (3 b x 128 rows),
-// one thread issues GEMM 1, all wait on an mbarrier (bounded), threads form
-// H^ and write A2, one thread issues GEMM 2, threads read H back into shared
-// memory.  Tensor memory columns (512 allocated per CTA):
+// block of tensor memory).  Per chunk: one thread issues GEMM 1 on the A1 rows
+// written before, all wait on an mbarrier (bounded; the product's tensor loads
+// go out first), threads form H^ and write A2, one thread issues GEMM 2, the
+// threads write the next chunk's A1 while it runs, then read H back into
+// shared memory.  Tensor memory columns (512 allocated per CTA):
 //   [0, 6 PZ)             D1: 3 b x 2 PZ  (re kz | im kz)
+//                         D2: 3 a x 2 NZ (re z | im z), in D1's first columns
+//                         (D1 has been read into registers when GEMM 2 starts)
 //   [6 PZ, 6 PZ + 6 NZ)   A1: 3 b x {hi, lo} x NZ columns (K = 2 NZ: re z | im z)
-//                         D2: 3 a x 2 NZ (re z | im z), reusing A1's columns
 //   [6 PZ + 6 NZ, ...)    A2: 3 a x {hi, lo} x PZ columns (K = 2 PZ: re kz | im kz)
 #pragma once
 #include <cuda_bf16.h>
@@ -159,7 +161,7 @@ struct Dft {
   static constexpr int B1 = N1 * K1 * 2, B2 = N2 * K2 * 2;
   static constexpr int bytes = 2 * B1 + 2 * B2;   // B1 hi, B1 lo, B2 hi, B2 lo
   static constexpr int KW = PZ / 4;               // kz values per thread in the product
-  static constexpr uint32_t D1 = 0, A1 = 6 * PZ, D2 = 6 * PZ, A2 = 6 * PZ + 6 * NZ;
+  static constexpr uint32_t D1 = 0, A1 = 6 * PZ, D2 = 0, A2 = 6 * PZ + 6 * NZ;
 };
 
 // Wait for phase `ph` of bar (bounded); false when it gave up.
@@ -182,11 +184,11 @@ __device__ __forceinline__ bool zprod_split(float2* buf, int rs, int nz, int py,
   const uint32_t lane_off = (uint32_t)(32 * q) << 16;  // this warp's tensor-memory lanes
   const uint32_t b1h = smem_u32(Bsm), b1l = b1h + G::B1, b2h = b1l + G::B1, b2l = b2h + G::B2;
   constexpr uint32_t id1 = idesc_f16(S::fmt, 128, G::N1), id2 = idesc_f16(S::fmt, 128, G::N2);
-  for (int ky0 = 0; ky0 < PY; ky0 += 128) {
-    const int ky = ky0 + 32 * q + lane;
-    const int pos = pidx<PADS>(ky);
-    // 1. A1 rows: (b = g, ky) -> K = 2 NZ reals (re z | im z), split, packed 2 per column
+  // 1. A1 rows of the chunk at ky0: (b = g, ky) -> K = 2 NZ reals (re z | im z),
+  //    split, packed 2 per column
+  auto fill_a1 = [&](int ky0) {
     if (g < 3) {
+      const int pos = pidx<PADS>(ky0 + 32 * q + lane);
       uint32_t hi[NZ], lo[NZ];
 #pragma unroll
       for (int c = 0; c < NZ; ++c) {
@@ -213,8 +215,13 @@ __device__ __forceinline__ bool zprod_split(float2* buf, int rs, int nz, int py,
       TmemIO<NZ>::st(ta + NZ, lo);
       wait_st();
     }
-    fence_before();
-    __syncthreads();
+  };
+  fill_a1(0);
+  fence_before();
+  __syncthreads();
+  for (int ky0 = 0; ky0 < PY; ky0 += 128) {
+    const int ky = ky0 + 32 * q + lane;
+    const int pos = pidx<PADS>(ky);
     // 2. GEMM 1: D1_b = A1_b * B1 (3 split terms per K step)
     if (tid == 0) {
       fence_after();
@@ -324,6 +331,9 @@ __device__ __forceinline__ bool zprod_split(float2* buf, int rs, int nz, int py,
       }
       mma_commit(bar);
     }
+    // the next chunk's A1 while GEMM 2 runs: GEMM 1 has completed (A1 is free) and
+    // GEMM 2 reads A2 and writes D2 in D1's columns, neither of which A1 overlaps
+    if (ky0 + 128 < PY) fill_a1(ky0 + 128);
     if (!wait_phase(bar, phase)) {
       if (tid == 0) atomicOr(flag + 1, 1);
       return false;
