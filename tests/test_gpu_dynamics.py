@@ -61,6 +61,25 @@ def test_short_trajectory_state_parity(integ):
     s.close()
 
 
+def test_short_trajectory_ragged_tiles_px512():
+    # px = 512 with a ragged last tile (150 = 18 x 8 + 6 rows) and 75 pairs of cells per row:
+    # the x kernel's tensor-copy tile path and two-pass transforms, and the z product's
+    # transform form (9 planes, py = 512)
+    import torch
+    grid = (150, 150, 9)
+    w = inputs.Workload("t", grid, 4e-9, inputs.Material(Ms=8e5, A=1.3e-11, Ku=5e4, alpha=0.05),
+                        (0.0, 0.0, 0.01), 5e-14, 20, "random", 98)
+    m0 = inputs.workload_state(w)
+    s = _solver_for(w)
+    s.set_m(torch.from_numpy(m0).cuda())
+    s.step(w.steps, w.dt)
+    mg = s.get_m().cpu().numpy()
+    film = _film_for(w)
+    mo = to_device(film.run(to_xyz(m0), w.dt, w.steps, "rk4"))
+    assert np.abs(mg - mo).max() <= 2e-5, np.abs(mg - mo).max()
+    s.close()
+
+
 def test_two_steps_full_size_256x256x16():
     import torch
     w = inputs.film_256x256x16()
