@@ -250,14 +250,30 @@ int mm_step_timed(mm_ctx* ctx, int n, double dt, double ms_out[3]);
  *                            (I - m0 m0^T) dL/dm0, i.e. through the
  *                            normalisation that mm_set_m applies
  * Memory: checkpoints every ckpt_every steps ((n/ckpt_every + 1) states) and
- * one recomputed segment (8 ckpt_every + 1 vector fields), allocated on the
- * first call and kept.  Cost: one forward pass, one recomputation, and four
- * applications of the symmetric exchange + demag operator per step.  RK4 only
- * (MM_EUNSUPPORTED for Euler or while a field program is installed: the
- * derivative assumes a constant uniform field and damping).  Asynchronous.
+ * R segment slots of 8 ckpt_every + 1 vector fields each (every stage state
+ * and field of a segment), allocated on the first call and kept.  The forward
+ * pass records its last R segments into the slots, so only the segments before
+ * them are recomputed from their checkpoints: R = 1 by default, more (at most
+ * 8, at most the number of segments) as far as mm_set_adjoint_memory allows.
+ * The gradients are the same bit for bit whatever R is.  Cost: one forward
+ * pass, one recomputation of the unrecorded segments, and four applications of
+ * the symmetric exchange + demag operator per step.  RK4 only (MM_EUNSUPPORTED
+ * for Euler or while a field program is installed: the derivative assumes a
+ * constant uniform field and damping).  Asynchronous.
  */
 int mm_adjoint(mm_ctx* ctx, int n, double dt, int ckpt_every, const float* dL_dm_final,
                float* dL_dh, float* dL_dku, float* dL_dm0);
+
+/*
+ * Device memory, in bytes, that mm_adjoint may give to recorded segments.  A
+ * slot holds 12 (8 ckpt_every + 1) N bytes (every stage state and field of one
+ * segment, N cells); mm_adjoint uses R = max(1, min(8, segments,
+ * floor(bytes / slot bytes))) slots.  0 (the default) keeps R = 1: every
+ * segment but the last is recomputed from its checkpoint.  A larger budget
+ * trades device memory for recomputation.  MM_EINVAL for a negative or NaN
+ * value.
+ */
+int mm_set_adjoint_memory(mm_ctx* ctx, double bytes);
 
 /*
  * Observables series (mm_opts.obs_every > 0): copies the most recent records

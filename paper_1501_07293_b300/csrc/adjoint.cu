@@ -20,7 +20,9 @@
 //     and lam_k3 += dt lam_s4, lam_k2 += dt/2 lam_s3, lam_k1 += dt/2 lam_s2.
 // The trajectory is kept as checkpoints every `ckpt_every` steps; each segment
 // is recomputed once with every stage state s_i and field B_i stored, then
-// swept in reverse.  Per reverse step: per stage the y/z pass and the x kernel
+// swept in reverse -- except the last R segments, which the forward pass
+// records directly (R = 1, or more within the memory budget of
+// mm_set_adjoint_memory).  Per reverse step: per stage the y/z pass and the x kernel
 // in its adjoint mode, which applies L to lam_B and does the closing and
 // opening updates of the stages in the same pass (StageArgs modes 3 - 5); the
 // closing kernel of a step also starts the previous step, so only a segment's
@@ -111,8 +113,23 @@ static int grow(mm_ctx* c, float** p, size_t* cap, size_t need_floats) {
   return MM_OK;
 }
 
+static void drop_adj_graphs(mm_ctx* c) {
+  for (int i = 0; i < 1 + 2 * kAdjSlots; ++i)
+    if (c->adj_graph[i]) {
+      cudaGraphExecDestroy(c->adj_graph[i]);
+      c->adj_graph[i] = nullptr;
+    }
+}
+
+extern "C" int mm_set_adjoint_memory(mm_ctx* c, double bytes) {
+  if (!c) return MM_EINVAL;
+  if (!(bytes >= 0)) return mm_fail(c, MM_EINVAL, "mm_set_adjoint_memory: bytes = %g", bytes);
+  c->adj_budget = bytes;
+  return MM_OK;
+}
+
 void mm_adjoint_free(mm_ctx* c) {
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 1 + 2 * kAdjSlots; ++i)
     if (c->adj_graph[i]) {
       cudaGraphExecDestroy(c->adj_graph[i]);
       c->adj_graph[i] = nullptr;
@@ -137,25 +154,30 @@ extern "C" int mm_adjoint(mm_ctx* c, int n, double dt, int ckpt_every, const flo
   const size_t v3 = 3 * (size_t)N;
   const int k = ckpt_every < n ? ckpt_every : n;
   const int nseg = (n + k - 1) / k;
+  // the forward pass records its last R segments (stage states and fields) in
+  // R slots of the segment buffer: the last one always, more while the slots
+  // fit the budget of mm_set_adjoint_memory; only the segments before them are
+  // recomputed from their checkpoints
+  const size_t slot = (size_t)(8 * k + 1) * v3;   // floats of one recorded segment
+  int R = (int)(c->adj_budget / ((double)slot * sizeof(float)));
+  if (R > nseg) R = nseg;
+  if (R > kAdjSlots) R = kAdjSlots;
+  if (R < 1) R = 1;
   int rc;
   float* const prev[3] = {c->adj_ckpt, c->adj_seg, c->adj_work};
   if ((rc = grow(c, &c->adj_ckpt, &c->adj_ckpt_cap, (size_t)(nseg + 1) * v3)) != MM_OK) return rc;
-  if ((rc = grow(c, &c->adj_seg, &c->adj_seg_cap, (size_t)(8 * k + 1) * v3)) != MM_OK) return rc;
+  if ((rc = grow(c, &c->adj_seg, &c->adj_seg_cap, (size_t)R * slot)) != MM_OK) return rc;
   if ((rc = grow(c, &c->adj_work, &c->adj_work_cap, 9 * v3 + (size_t)N)) != MM_OK) return rc;
-  if (prev[0] != c->adj_ckpt || prev[1] != c->adj_seg || prev[2] != c->adj_work)
-    for (int i = 0; i < 3; ++i)
-      if (c->adj_graph[i]) {
-        cudaGraphExecDestroy(c->adj_graph[i]);
-        c->adj_graph[i] = nullptr;
-      }
+  if (prev[0] != c->adj_ckpt || prev[1] != c->adj_seg || prev[2] != c->adj_work) drop_adj_graphs(c);
   float* W = c->adj_work;
   float *lam = W, *lam_m = W + v3, *lk0 = W + 2 * v3, *lk1 = W + 3 * v3, *lk2 = W + 4 * v3;
   float *lamB = W + 5 * v3, *lamloc = W + 6 * v3, *lamB2 = W + 7 * v3, *gh = W + 8 * v3, *gku = W + 9 * v3;
   // (lamB2: the other lam_B buffer of the fused sweep, ping-pong)
-  float* seg_s = c->adj_seg;                   // [k][4][3N] stage states, then [1][3N] the segment's end
-  // (the workspace addresses are baked into the segment graph: a workspace that
-  // grows is a new allocation, so the graph is dropped then)
-  float* seg_B = c->adj_seg + (size_t)(4 * k + 1) * v3;   // [k][4][3N] fields
+  // slot r: [k][4][3N] stage states, then [1][3N] the segment's end, then
+  // [k][4][3N] fields (the workspace addresses are baked into the segment
+  // graphs: a workspace that grows is a new allocation, so they are dropped then)
+  auto seg_s = [&](int r) { return c->adj_seg + (size_t)r * slot; };
+  auto seg_B = [&](int r) { return c->adj_seg + (size_t)r * slot + (size_t)(4 * k + 1) * v3; };
   cudaStream_t s = c->stream;
 
   const Phys ph = [&] {
@@ -190,21 +212,22 @@ extern "C" int mm_adjoint(mm_ctx* c, int n, double dt, int ckpt_every, const flo
   // A segment's recording: from its start state in seg_s, len RK4 steps with
   // every stage state and field stored (ticks: the steps advance the context's
   // clock and step count, as mm_step's do).  Enqueued on stream q.
-  auto enqueue_record = [&](cudaStream_t q, int len, bool ticks, long long* nk) -> int {
+  auto enqueue_record = [&](cudaStream_t q, int r, int len, bool ticks, long long* nk) -> int {
     *nk = 0;
-    if (launch_xfwd(dA, seg_s, c->tw, c->S, q) < 0) return mm_fail(c, MM_ECUDA, "adjoint: x-transform launch failed");
+    float* const ss = seg_s(r);
+    if (launch_xfwd(dA, ss, c->tw, c->S, q) < 0) return mm_fail(c, MM_ECUDA, "adjoint: x-transform launch failed");
     *nk += 1;
     StageArgs a = {};
     a.hmap = c->hmap; a.kumap = c->kumap; a.mode = 1; a.dt = (float)dt; a.acc = c->acc;
     for (int j = 0; j < len; ++j) {
-      float* sj = seg_s + (size_t)4 * j * v3;
+      float* sj = ss + (size_t)4 * j * v3;
       a.m0 = sj;
       for (int st = 0; st < 4; ++st) {
         a.stage = st;
         a.tick = (ticks && st == 0) ? Tick{c->prog, dt, 0} : Tick{};
         a.m_in = sj + st * v3;
-        a.m_out = st < 3 ? sj + (st + 1) * v3 : seg_s + (size_t)4 * (j + 1) * v3;
-        a.B_out = seg_B + ((size_t)4 * j + st) * v3;
+        a.m_out = st < 3 ? sj + (st + 1) * v3 : ss + (size_t)4 * (j + 1) * v3;
+        a.B_out = seg_B(r) + ((size_t)4 * j + st) * v3;
         const int kk = launch_stage(dA, ph, a, c->tw, c->S, c->Kh, c->dflag, q);
         if (kk < 0) return mm_fail(c, MM_ECUDA, "adjoint: stage kernels failed to launch");
         *nk += kk;
@@ -212,7 +235,7 @@ extern "C" int mm_adjoint(mm_ctx* c, int n, double dt, int ckpt_every, const flo
     }
     return MM_OK;
   };
-  auto enqueue_sweep = [&](cudaStream_t q, int len, long long* nk) -> int {
+  auto enqueue_sweep = [&](cudaStream_t q, int r, int len, long long* nk) -> int {
     *nk = 0;
     // the reverse sweep of the segment: one pointwise kernel starts its last step
     // (k_adj_start), then per step and stage one y/z pass and one x kernel that
@@ -221,8 +244,8 @@ extern "C" int mm_adjoint(mm_ctx* c, int n, double dt, int ckpt_every, const flo
     // (mode 5), except for the segment's first step (mode 4)
     auto step_fields = [&](int j, const float** sq, const float** Bq) {
       for (int st = 0; st < 4; ++st) {
-        sq[st] = seg_s + ((size_t)4 * j + st) * v3;
-        Bq[st] = seg_B + ((size_t)4 * j + st) * v3;
+        sq[st] = seg_s(r) + ((size_t)4 * j + st) * v3;
+        Bq[st] = seg_B(r) + ((size_t)4 * j + st) * v3;
       }
     };
     {
@@ -272,19 +295,18 @@ extern "C" int mm_adjoint(mm_ctx* c, int n, double dt, int ckpt_every, const flo
     return MM_OK;
   };
   // full-length segments replay captured graphs (rebuilt when the segment
-  // length, dt or the context's field, damping or launch shapes changed)
-  if (c->adj_graph_len != k || c->adj_graph_dt != dt || c->adj_graph_gen != c->param_gen)
-    for (int i = 0; i < 3; ++i)
-      if (c->adj_graph[i]) {
-        cudaGraphExecDestroy(c->adj_graph[i]);
-        c->adj_graph[i] = nullptr;
-      }
-  for (int gi = 0; gi < 3; ++gi) {
-    if (c->adj_graph[gi]) continue;
+  // length, dt or the context's field, damping or launch shapes changed);
+  // graph 0 recomputes into slot 0, 1 + r records slot r in the forward pass,
+  // 1 + kAdjSlots + r sweeps slot r
+  if (c->adj_graph_len != k || c->adj_graph_dt != dt || c->adj_graph_gen != c->param_gen) drop_adj_graphs(c);
+  auto graph_of = [&](int gi) -> int {
+    if (c->adj_graph[gi]) return MM_OK;
     cudaGraph_t graph;
     long long nk = 0;
     MM_CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const int r = gi < 2 ? enqueue_record(c->cap_stream, k, gi == 1, &nk) : enqueue_sweep(c->cap_stream, k, &nk);
+    const int r = gi == 0 ? enqueue_record(c->cap_stream, 0, k, false, &nk)
+                : gi <= kAdjSlots ? enqueue_record(c->cap_stream, gi - 1, k, true, &nk)
+                                  : enqueue_sweep(c->cap_stream, gi - 1 - kAdjSlots, k, &nk);
     const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
     if (r != MM_OK || e != cudaSuccess) {
       cudaGetLastError();
@@ -297,48 +319,66 @@ extern "C" int mm_adjoint(mm_ctx* c, int n, double dt, int ckpt_every, const flo
       return mm_fail(c, MM_ECUDA, "adjoint: segment graph instantiate failed: %s", cudaGetErrorString(ei));
     }
     c->adj_graph_nodes[gi] = nk;
+    MM_CK(c, cudaGraphUpload(c->adj_graph[gi], c->stream));
+    return MM_OK;
+  };
+  if ((rc = graph_of(0)) != MM_OK) return rc;
+  for (int r = 0; r < R; ++r) {
+    if ((rc = graph_of(1 + r)) != MM_OK) return rc;
+    if ((rc = graph_of(1 + kAdjSlots + r)) != MM_OK) return rc;
   }
   c->adj_graph_len = k;
   c->adj_graph_dt = dt;
   c->adj_graph_gen = c->param_gen;
-  auto run = [&](int gi, int len) -> int {   // a full-length segment from its graph, else eagerly
+  // kind 0: recompute into slot 0, 1: record slot r in the forward pass, 2: sweep slot r
+  auto run = [&](int kind, int r, int len) -> int {   // a full-length segment from its graph, else eagerly
+    const int gi = kind == 0 ? 0 : kind == 1 ? 1 + r : 1 + kAdjSlots + r;
     if (len == k) {
       MM_CK(c, cudaGraphLaunch(c->adj_graph[gi], s));
       c->launches += c->adj_graph_nodes[gi];
       return MM_OK;
     }
     long long nk = 0;
-    const int r = gi < 2 ? enqueue_record(s, len, gi == 1, &nk) : enqueue_sweep(s, len, &nk);
+    const int rr = kind == 2 ? enqueue_sweep(s, r, len, &nk) : enqueue_record(s, r, len, kind == 1, &nk);
     c->launches += nk;
-    return r;
+    return rr;
   };
 
-  // 1. forward n steps from the current state, a checkpoint every k steps; the
-  //    last segment is recorded on the way (its stage states and fields are the
-  //    first the reverse sweep needs), so it is not recomputed
+  // 1. forward n steps from the current state, a checkpoint every k steps up to
+  //    the recorded segments; the last R segments are recorded on the way (their
+  //    stage states and fields are the first the reverse sweep needs), so they
+  //    are not recomputed.  Only the last segment can be shorter than k.
+  const int g0 = nseg - R;   // first recorded segment
   MM_CK(c, cudaMemcpyAsync(c->adj_ckpt, c->m0, v3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
-  for (int g = 0; g < nseg - 1; ++g) {
+  for (int g = 0; g < g0; ++g) {
     if ((rc = mm_step(c, k, dt)) != MM_OK) return rc;
     MM_CK(c, cudaMemcpyAsync(c->adj_ckpt + (size_t)(g + 1) * v3, c->m0, v3 * sizeof(float),
                              cudaMemcpyDeviceToDevice, s));
   }
   const int len_last = n - (nseg - 1) * k;
-  MM_CK(c, cudaMemcpyAsync(seg_s, c->m0, v3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
-  if ((rc = run(1, len_last)) != MM_OK) return rc;
-  const float* m_final = seg_s + (size_t)4 * len_last * v3;
+  for (int r = 0; r < R; ++r) {
+    const float* start = r == 0 ? c->m0 : seg_s(r - 1) + (size_t)4 * k * v3;
+    MM_CK(c, cudaMemcpyAsync(seg_s(r), start, v3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    const int len = r == R - 1 ? len_last : k;
+    if ((rc = run(1, r, len)) != MM_OK) return rc;
+    c->steps += len;
+  }
+  const float* m_final = seg_s(R - 1) + (size_t)4 * len_last * v3;
   MM_CK(c, cudaMemcpyAsync(c->m0, m_final, v3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
   MM_CK(c, cudaMemcpyAsync(c->adj_ckpt + (size_t)nseg * v3, m_final, v3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
-  c->steps += len_last;
-  // 2. reverse sweep, segment by segment
+  // 2. reverse sweep, segment by segment: the recorded slots first, then each
+  //    earlier segment recomputed from its checkpoint into slot 0
   MM_CK(c, cudaMemcpyAsync(lam, dL_dm_final, v3 * sizeof(float), cudaMemcpyDefault, s));
   MM_CK(c, cudaMemsetAsync(gh, 0, (v3 + N) * sizeof(float), s));
   for (int g = nseg - 1; g >= 0; --g) {
     const int len = (g + 1) * k <= n ? k : n - g * k;
-    if (g < nseg - 1) {
-      MM_CK(c, cudaMemcpyAsync(seg_s, c->adj_ckpt + (size_t)g * v3, v3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
-      if ((rc = run(0, len)) != MM_OK) return rc;
+    int r = g - g0;
+    if (g < g0) {
+      r = 0;
+      MM_CK(c, cudaMemcpyAsync(seg_s(0), c->adj_ckpt + (size_t)g * v3, v3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      if ((rc = run(0, 0, len)) != MM_OK) return rc;
     }
-    if ((rc = run(2, len)) != MM_OK) return rc;
+    if ((rc = run(2, r, len)) != MM_OK) return rc;
   }
   c->s_valid = 0;   // S was used as scratch
   // 3. outputs

@@ -90,7 +90,7 @@ static void make_xmap(mm_ctx* c) {
 }
 
 static void drop_graphs(mm_ctx* c) {
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 4; ++i)
     if (c->graph[i]) {
       cudaGraphExecDestroy(c->graph[i]);
       c->graph[i] = nullptr;
@@ -475,17 +475,33 @@ static int ensure_spectrum(mm_ctx* c) {
   return MM_OK;
 }
 
+// Steps per graph of the long form: mm_step replays whole graphs of this many
+// steps (an even count, so Euler's alternating buffers end where they began)
+// and single steps for the rest, so consecutive steps are joined by the graph's
+// own edges rather than by a graph launch each.
+static constexpr int kStepsPerGraph = 16;
+
 // Capture the step sequence.  An existing executable graph of the same shape
 // (only kernel parameters changed: dt, the field, the damping, map pointers)
-// is updated in place; otherwise it is instantiated anew.
+// is updated in place; otherwise it is instantiated anew.  graph[g] holds one
+// step from buffer g, graph[2 + g] kStepsPerGraph steps from it.
 static int build_graphs(mm_ctx* c, double dt) {
   if (c->graph_integrator != c->opts.integrator) drop_graphs(c);
-  const int ng = c->opts.integrator == MM_EULER ? 2 : 1;
-  for (int g = 0; g < ng; ++g) {
+  const bool euler = c->opts.integrator == MM_EULER;
+  const int ng = euler ? 2 : 1;
+  for (int gi = 0; gi < 2 * ng; ++gi) {
+    const int g = gi < ng ? gi : 2 + (gi - ng);   // slot: 0, (1,) 2, (3)
+    const int from = g & 1;
+    const int nsteps = g >= 2 ? kStepsPerGraph : 1;
     cudaGraph_t graph;
     MM_CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     long long nk = 0;
-    const int r = enqueue_step(c, c->cap_stream, dt, g, &nk);
+    int r = 0;
+    for (int i = 0; i < nsteps && r >= 0; ++i) {
+      long long k1 = 0;
+      r = enqueue_step(c, c->cap_stream, dt, euler ? (from + i) & 1 : 0, &k1);
+      nk += k1;
+    }
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
     if (r < 0 || e != cudaSuccess) {
       cudaGetLastError();
@@ -513,6 +529,8 @@ static int build_graphs(mm_ctx* c, double dt) {
     }
     cudaGraphDestroy(graph);
     c->graph_nodes[g] = nk;
+    // upload now, so the first replay inside a caller's timed loop does not pay for it
+    MM_CK(c, cudaGraphUpload(c->graph[g], c->stream));
   }
   c->graph_valid = 1;
   c->graph_dt = dt;
@@ -534,11 +552,18 @@ extern "C" int mm_step(mm_ctx* c, int n, double dt) {
     const int r = ensure_spectrum(c);
     if (r != MM_OK) return r;
   }
-  for (int i = 0; i < n; ++i) {
-    const int g = c->opts.integrator == MM_EULER ? c->cur : 0;
+  const bool euler = c->opts.integrator == MM_EULER;
+  int i = 0;
+  for (; i + kStepsPerGraph <= n; i += kStepsPerGraph) {   // an even count: Euler's buffer is unchanged
+    const int g = 2 + (euler ? c->cur : 0);
     MM_CK(c, cudaGraphLaunch(c->graph[g], c->stream));
     c->launches += c->graph_nodes[g];
-    if (c->opts.integrator == MM_EULER) c->cur ^= 1;
+  }
+  for (; i < n; ++i) {
+    const int g = euler ? c->cur : 0;
+    MM_CK(c, cudaGraphLaunch(c->graph[g], c->stream));
+    c->launches += c->graph_nodes[g];
+    if (euler) c->cur ^= 1;
   }
   c->steps += n;
   return MM_OK;

@@ -160,6 +160,9 @@ struct StageArgs {
   float dt;
 };
 
+// most segments mm_adjoint keeps recorded from its forward pass
+static constexpr int kAdjSlots = 8;
+
 struct mm_ctx {
   Dims d;
   double delta, Ms, A, Ku, alpha, gamma;
@@ -187,21 +190,24 @@ struct mm_ctx {
   int prog_n;                // segments installed
   int cur;                   // Euler: 0 -> state in m0, 1 -> state in stA
   int s_valid;               // S holds the x transform of the current state
-  cudaGraphExec_t graph[2];  // RK4: graph[0]; Euler: graph[0] (m0->stA), graph[1] (stA->m0)
+  cudaGraphExec_t graph[4];  // RK4: graph[0]; Euler: graph[0] (m0->stA), graph[1] (stA->m0);
+                             // graph[2 + g]: kStepsPerGraph steps from the start of graph[g]
   int graph_valid;
   double graph_dt;
   int graph_integrator;
-  long long graph_nodes[2];
+  long long graph_nodes[4];
   long long launches;
   long long steps;
   long long param_gen;        // bumped whenever the field, damping, program or launch shapes change
-  // adjoint: captured graphs of a full-length segment's recording (recomputed:
-  // [0], in the forward pass with the clock advancing: [1]) and reverse sweep [2]
-  cudaGraphExec_t adj_graph[3];
+  // adjoint: captured graphs of a full-length segment, per slot r of the
+  // segment buffer: [0] the recomputation into slot 0, [1 + r] the recording in
+  // the forward pass (the clock advancing), [1 + kAdjSlots + r] the reverse sweep
+  cudaGraphExec_t adj_graph[1 + 2 * kAdjSlots];
   int adj_graph_len;
   double adj_graph_dt;
   long long adj_graph_gen;
-  long long adj_graph_nodes[3];
+  long long adj_graph_nodes[1 + 2 * kAdjSlots];
+  double adj_budget;          // bytes of recorded segments the forward pass may keep (mm_set_adjoint_memory)
   // adjoint workspace (allocated by the first mm_adjoint, grown on demand)
   float* adj_ckpt;           // checkpoints [nseg + 1][3N]
   float* adj_seg;            // stage states [k][4][3N] + end state [3N], then fields [k][4][3N]

@@ -70,6 +70,7 @@ _SIGNATURES = {
     "mm_observables": (_I, [_P, ctypes.POINTER(_D)]),
     "mm_step_timed": (_I, [_P, _I, _D, ctypes.POINTER(_D)]),
     "mm_adjoint": (_I, [_P, _I, _D, _I, _P, _P, _P, _P]),
+    "mm_set_adjoint_memory": (_I, [_P, _D]),
     "mm_get_series": (_I, [_P, _P, _I, ctypes.POINTER(_I)]),
     "mm_set_tuning": (_I, [_P, _I, _I]),
     "mm_get_tuning": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
@@ -287,6 +288,10 @@ class Solver:
             if v is not None:
                 out[k] = v
         return out
+
+    def set_adjoint_memory(self, nbytes: float):
+        """mm_set_adjoint_memory: bytes of recorded segments mm_adjoint's forward pass may keep."""
+        self._check(self._L.mm_set_adjoint_memory(self.ctx, float(nbytes)))
 
     def energy(self) -> np.ndarray:
         e = (_D * 5)()

@@ -93,6 +93,47 @@ def test_adjoint_is_independent_of_checkpoint_spacing():
             assert np.array_equal(got[key], ref[key]), (k, key)
 
 
+def test_recorded_segments_give_the_same_gradients_bit_for_bit():
+    # mm_set_adjoint_memory lets the forward pass record more trailing segments
+    # (R = 1, 3, then all 7 of 47 steps at a checkpoint every 7, the last one
+    # ragged); the sweep sees the same stage data, so every output and the
+    # final state must equal the default's exactly, on one context in a row
+    import torch
+    w = inputs.film_16x8x1()
+    mat = w.mat
+    grid = w.grid
+    n, k = 47, 7
+    s = make_solver(grid, w.delta, Ms=mat.Ms, A=mat.A, Ku=0.0, alpha=mat.alpha, gamma=mat.gamma)
+    s.set_field((0.0, 0.0, 0.0), torch.from_numpy(inputs.zeeman_map(grid, 5201)).cuda(),
+                torch.from_numpy(inputs.ku_map(grid, 5202)).cuda())
+    m0 = torch.from_numpy(inputs.workload_state(w)).cuda()
+    g = torch.full((3, grid[2], grid[1], grid[0]), 1e-3, dtype=torch.float32, device="cuda")
+    slot = 12 * (8 * k + 1) * grid[0] * grid[1] * grid[2]
+    runs = []
+    for budget in (0, 3 * slot, 1e12, 0):
+        s.set_adjoint_memory(budget)
+        s.set_m(m0)
+        gr = s.adjoint(n, w.dt, k, g)
+        runs.append(({key: v.cpu().numpy() for key, v in gr.items()}, s.get_m().cpu().numpy()))
+    s.close()
+    ref, mref = runs[0]
+    for got, mf in runs[1:]:
+        assert np.array_equal(mf, mref)
+        for key in ref:
+            assert np.isfinite(got[key]).all()
+            assert np.array_equal(got[key], ref[key]), key
+
+
+def test_adjoint_memory_rejects_bad_budgets():
+    from paper_1501_07293_b300.solver import MM_EINVAL, MMError
+    s = make_solver((8, 4, 1), 4e-9, Ms=8e5, A=1.3e-11, Ku=0.0, alpha=0.02, gamma=1.76e11)
+    for bad in (-1.0, float("nan")):
+        with pytest.raises(MMError) as e:
+            s.set_adjoint_memory(bad)
+        assert e.value.code == MM_EINVAL
+    s.close()
+
+
 def test_autograd_wrapper_full_size_directional_fd():
     # the differentiation study at full size: 128x128x4, 500 RK4 steps, checkpoint every 50
     import torch
