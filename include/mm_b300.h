@@ -129,8 +129,12 @@ int mm_padded_dims(const mm_ctx* ctx, int padded[3]);
 
 /*
  * Set the state from m (host or device, [3][nz][ny][nx] float32).  Each cell's
- * vector is normalised on entry; a zero or non-finite vector gives
- * MM_ENONFINITE when it is detected (at the next synchronising call).
+ * vector is normalised on entry; a zero or non-finite vector is kept as given
+ * and gives MM_ENONFINITE when it is detected (at the next synchronising call).
+ * Page-locked host memory (cudaHostAlloc / cudaHostRegister) is read directly
+ * by the normalising kernel when N is a multiple of 4; other memory is copied
+ * first.  Asynchronous either way: m must stay unchanged until the stream has
+ * passed this call.
  */
 int mm_set_m(mm_ctx* ctx, const float* m);
 

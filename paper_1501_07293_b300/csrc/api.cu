@@ -1,6 +1,7 @@
 // C ABI of libmm_b300 (declared in include/mm_b300.h): context life cycle,
 // state and field set-up, the captured step graph, energies and observables.
 #include <stdarg.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -322,8 +323,21 @@ extern "C" int mm_set_m(mm_ctx* c, const float* m) {
   if (!m) return mm_fail(c, MM_EINVAL, "mm_set_m: m is NULL");
   c->cur = 0;
   c->s_valid = 0;
-  MM_CK(c, cudaMemcpyAsync(c->m0, m, sizeof(float) * 3 * (size_t)c->d.N, cudaMemcpyDefault, c->stream));
-  if (launch_normalise(c->d, c->m0, c->dflag, c->stream) < 0) return mm_fail(c, MM_ECUDA, "normalise launch failed");
+  // page-locked host memory: the normalising kernel reads it over the bus
+  // directly (the SMs keep many more reads in flight than one copy engine);
+  // device or pageable memory: one copy, then normalisation in place
+  cudaPointerAttributes at;
+  const bool pinned = cudaPointerGetAttributes(&at, m) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                      at.devicePointer != nullptr && (c->d.N % 4) == 0 &&
+                      ((uintptr_t)at.devicePointer % 16) == 0;
+  cudaGetLastError();   // a pointer the runtime does not know (pageable) is not an error here
+  if (pinned) {
+    if (launch_normalise_from(c->d, (const float*)at.devicePointer, c->m0, c->dflag, c->stream) < 0)
+      return mm_fail(c, MM_ECUDA, "normalise launch failed");
+  } else {
+    MM_CK(c, cudaMemcpyAsync(c->m0, m, sizeof(float) * 3 * (size_t)c->d.N, cudaMemcpyDefault, c->stream));
+    if (launch_normalise(c->d, c->m0, c->dflag, c->stream) < 0) return mm_fail(c, MM_ECUDA, "normalise launch failed");
+  }
   c->launches++;
   c->steps = 0;
   // the step count (and the observables series) restarts with the new state

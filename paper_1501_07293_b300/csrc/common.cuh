@@ -328,6 +328,8 @@ int launch_xfwd(const Dims& d, const float* m, const float2* tw, float2* S, cuda
 int launch_field_part(const Dims& d, const Phys& ph, const StageArgs& a, const float2* tw, float2* S,
                       const float* Kh, int* flag, cudaStream_t s, int part);
 int launch_normalise(const Dims& d, float* m, int* flag, cudaStream_t s);
+// dst <- src normalised (N % 4 == 0, both 16-byte aligned); src may be page-locked host memory
+int launch_normalise_from(const Dims& d, const float* src, float* dst, int* flag, cudaStream_t s);
 
 // reduce.cu
 // drive: if set, bx, by, bz, g1, g2 (device) replacing Phys's

@@ -27,6 +27,37 @@ __global__ void k_normalise(float* __restrict__ m, long long N, int* flag) {
   m[i + 2 * N] = z * inv;
 }
 
+// k_normalise_from: dst <- src / |src|, four cells per thread; src may be page-
+// locked host memory that the kernel reads over the bus (the SMs' many
+// outstanding loads, instead of one copy engine).  A zero or non-finite vector
+// is flagged and passed through unchanged, as k_normalise leaves it.
+__global__ void k_normalise_from(const float4* __restrict__ src, float4* __restrict__ dst, long long N4, int* flag) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N4) return;
+  const float4 x = src[i], y = src[i + N4], z = src[i + 2 * N4];
+  float4 o[3];
+  const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w}, zs[4] = {z.x, z.y, z.z, z.w};
+  float r[3][4];
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float n2 = xs[j] * xs[j] + ys[j] * ys[j] + zs[j] * zs[j];
+    if (!(n2 > 0.f) || !isfinite(n2)) {
+      bad = true;
+      r[0][j] = xs[j]; r[1][j] = ys[j]; r[2][j] = zs[j];
+      continue;
+    }
+    const float inv = rsqrtf(n2);
+    r[0][j] = xs[j] * inv; r[1][j] = ys[j] * inv; r[2][j] = zs[j] * inv;
+  }
+  if (bad) atomicOr(flag, 1);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) o[c] = make_float4(r[c][0], r[c][1], r[c][2], r[c][3]);
+  dst[i] = o[0];
+  dst[i + N4] = o[1];
+  dst[i + 2 * N4] = o[2];
+}
+
 // ---------------------------------------------------------------------------
 // launch geometry
 // ---------------------------------------------------------------------------
@@ -205,6 +236,13 @@ int launch_field_part(const Dims& d, const Phys& ph, const StageArgs& a, const f
   }
   if (e != cudaSuccess) return -1;
   return part == 1 ? mm_yz_launches(d) : 1;
+}
+
+int launch_normalise_from(const Dims& d, const float* src, float* dst, int* flag, cudaStream_t s) {
+  const long long N4 = d.N / 4;
+  k_normalise_from<<<(unsigned)((N4 + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(src),
+                                                                 reinterpret_cast<float4*>(dst), N4, flag);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_normalise(const Dims& d, float* m, int* flag, cudaStream_t s) {
