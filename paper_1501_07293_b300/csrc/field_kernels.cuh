@@ -1088,6 +1088,163 @@ __device__ __forceinline__ void cell_updateV(const StageArgs& a, const Phys& ph,
   }
 }
 
+// The adjoint modes (3-5) of cell_update for V consecutive cells x0 .. x0+V-1
+// (nx a multiple of V): the same per-cell arithmetic, with V-wide loads and
+// stores of every field it touches.  m_in holds lam_B; nm returns what the
+// scalar form returns (lam_B of the next application of L, or, in mode 4, the
+// cells' own input).
+template <int V, bool PC = false>
+__device__ __forceinline__ void cell_adjV(const StageArgs& a, const Phys& ph, const Dims& d, int x0, int y, int z,
+                                          const float3 (&bd)[V], float3 (&nm)[V]) {
+  using Vec = VecOf<V>;
+  using T = typename Vec::T;
+  const long long N = d.N;
+  const long long cell = ((long long)z * d.ny + y) * d.nx + x0;
+  if (!MM_BC(x0 + V <= d.nx && y < d.ny && z < d.nz)) {
+#pragma unroll
+    for (int j = 0; j < V; ++j) nm[j] = make_float3(0.f, 0.f, 0.f);
+    return;
+  }
+  auto ld3 = [&](const float* p, float (&o)[3][V]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Vec::get(ld_rw<PC>(reinterpret_cast<const T*>(p + cell + c * N)), o[c]);
+  };
+  auto st3 = [&](float* p, const float (&v)[3][V]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) *reinterpret_cast<T*>(p + cell + c * N) = Vec::make(v[c]);
+  };
+  const long long row = d.nx, pl = (long long)d.nx * d.ny;
+  const long long oym = y > 0 ? -row : 0, oyp = y < d.ny - 1 ? row : 0;
+  const long long ozm = z > 0 ? -pl : 0, ozp = z < d.nz - 1 ? pl : 0;
+  float mv[3][V], L[3][V];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float* b = a.m_in + cell + c * N;
+    float sv[V + 2], vym[V], vyp[V], vzm[V], vzp[V];
+    Vec::get(ld_ro<PC>(reinterpret_cast<const T*>(b)), sv + 1);
+    sv[0] = x0 > 0 ? ld_ro<PC>(b - 1) : sv[1];
+    sv[V + 1] = x0 + V < d.nx ? ld_ro<PC>(b + V) : sv[V];
+    Vec::get(ld_ro<PC>(reinterpret_cast<const T*>(b + oym)), vym);
+    Vec::get(ld_ro<PC>(reinterpret_cast<const T*>(b + oyp)), vyp);
+    Vec::get(ld_ro<PC>(reinterpret_cast<const T*>(b + ozm)), vzm);
+    Vec::get(ld_ro<PC>(reinterpret_cast<const T*>(b + ozp)), vzp);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const float m = sv[j + 1];
+      mv[c][j] = m;
+      const float lap = ((sv[j] - m) + (sv[j + 2] - m)) + ((vym[j] - m) + (vyp[j] - m)) + ((vzm[j] - m) + (vzp[j] - m));
+      L[c][j] = ph.c_ex * lap + (c == 0 ? bd[j].x : c == 1 ? bd[j].y : bd[j].z);
+    }
+  }
+  float can[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) can[j] = ph.c_an;
+  if (a.kumap) {
+    float ku[V];
+    Vec::get(__ldg(reinterpret_cast<const T*>(a.kumap + cell)), ku);
+#pragma unroll
+    for (int j = 0; j < V; ++j) can[j] = ph.c_an_map * ku[j];
+  }
+  // ls = loc + L lam_B closes the stage; lm = lam_m + ls
+  float ls[3][V], lm[3][V];
+  ld3(a.adj_loc, ls);
+  ld3(a.adj_lam_m, lm);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      ls[c][j] = ls[c][j] + L[c][j];
+      lm[c][j] = lm[c][j] + ls[c][j];
+    }
+  if (a.mode == 4) {
+    st3(a.adj_lam, lm);
+#pragma unroll
+    for (int j = 0; j < V; ++j) nm[j] = make_float3(mv[0][j], mv[1][j], mv[2][j]);
+    return;
+  }
+  float lamB[3][V], loc[3][V];
+  if (a.mode == 5) {   // lm is the cotangent of the previous step's end state: start its sweep
+    float lu[3][V], sx3[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      float3 sq[4], Bq[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float s3[3][V], b3[3][V];
+        ld3(a.adj_sq[q], s3);
+        ld3(a.adj_Bq[q], b3);
+        sq[q] = make_float3(s3[0][j], s3[1][j], s3[2][j]);
+        Bq[q] = make_float3(b3[0][j], b3[1][j], b3[2][j]);
+      }
+      float3 u, lb, lc;
+      adj_step_start(ph.g1, ph.g2, can[j], a.adj_dt, sq, Bq, make_float3(lm[0][j], lm[1][j], lm[2][j]), u, lb, lc);
+      lu[0][j] = u.x; lu[1][j] = u.y; lu[2][j] = u.z;
+      lamB[0][j] = lb.x; lamB[1][j] = lb.y; lamB[2][j] = lb.z;
+      loc[0][j] = lc.x; loc[1][j] = lc.y; loc[2][j] = lc.z;
+      sx3[j] = sq[3].x;
+    }
+    const float h = a.adj_dt * (1.0f / 6.0f);
+    st3(a.adj_lam_m, lu);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float f = q == 0 ? h : 2.f * h;   // lk_1 = dt/6 lu, lk_2 = lk_3 = dt/3 lu
+      float lk[3][V];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int j = 0; j < V; ++j) lk[c][j] = f * lu[c][j];
+      st3(a.adj_lk0 + 3 * N * q, lk);
+    }
+    st3(a.adj_loc, loc);
+    float gh[3][V], gk[V];
+    ld3(a.adj_gh, gh);
+    Vec::get(ld_rw<PC>(reinterpret_cast<const T*>(a.adj_gku + cell)), gk);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) gh[c][j] += lamB[c][j];
+      gk[j] += ph.c_an_map * sx3[j] * lamB[0][j];   // c_an_map = 2 / Ms
+    }
+    st3(a.adj_gh, gh);
+    *reinterpret_cast<T*>(a.adj_gku + cell) = Vec::make(gk);
+  } else {             // mode 3: close this stage, open the next one
+    st3(a.adj_lam_m, lm);
+    float lk[3][V], sv[3][V], Bv[3][V];
+    ld3(a.adj_lk, lk);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int j = 0; j < V; ++j) lk[c][j] = lk[c][j] + a.adj_c * ls[c][j];
+    st3(a.adj_lk, lk);
+    // the VJP of eq. 2 at the next stage's recorded state and field
+    ld3(a.adj_s, sv);
+    ld3(a.adj_B, Bv);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      float3 lb, lc;
+      llg_vjp(ph.g1, ph.g2, can[j], make_float3(sv[0][j], sv[1][j], sv[2][j]),
+              make_float3(Bv[0][j], Bv[1][j], Bv[2][j]), make_float3(lk[0][j], lk[1][j], lk[2][j]), lb, lc);
+      lamB[0][j] = lb.x; lamB[1][j] = lb.y; lamB[2][j] = lb.z;
+      loc[0][j] = lc.x; loc[1][j] = lc.y; loc[2][j] = lc.z;
+    }
+    st3(a.adj_loc, loc);
+    float gh[3][V], gk[V];
+    ld3(a.adj_gh, gh);
+    Vec::get(ld_rw<PC>(reinterpret_cast<const T*>(a.adj_gku + cell)), gk);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) gh[c][j] += lamB[c][j];
+      gk[j] += ph.c_an_map * sv[0][j] * lamB[0][j];   // c_an_map = 2 / Ms
+    }
+    st3(a.adj_gh, gh);
+    *reinterpret_cast<T*>(a.adj_gku + cell) = Vec::make(gk);
+  }
+  st3(a.m_out, lamB);
+#pragma unroll
+  for (int j = 0; j < V; ++j) nm[j] = make_float3(lamB[0][j], lamB[1][j], lamB[2][j]);
+}
+
 // ---------------------------------------------------------------------------
 // k_x: CTA = (tile of TY rows along y, plane z), all three components.
 // Inverse x transform of the field (complex-to-real, first nx points), the
@@ -1189,7 +1346,7 @@ __device__ __forceinline__ void x16_forward(float2* rows, int RS, const float2* 
 // TMA: the S tile arrives as two tiled tensor copies (kx 0..128 and 129..257)
 // into a staging area [kx][c][TY] (xmap: the tensor map of S), instead of
 // per-thread copies; the C2R pre-processing then reads the staging area.
-template <int HALF, int TYV = XTile<HALF>::v, bool TMA = false, bool PC = false>
+template <int HALF, int TYV = XTile<HALF>::v, bool TMA = false, bool PC = false, bool ADJ = false>
 __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float2* __restrict__ S,
                                        const float2* __restrict__ twP, const Dims& d, int TY, int fwd, int z,
                                        int y0, const CUtensorMap* xmap = nullptr) {
@@ -1321,8 +1478,9 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
     }
     __syncthreads();
     float kmax = 0.f;
-    if ((a.mode == 1 || a.mode == 2) && (d.nx % XV) == 0) {
-      // XV consecutive cells per thread (vector loads and stores)
+    if ((a.mode == 1 || a.mode == 2 || (ADJ && a.mode >= 3)) && (d.nx % XV) == 0) {
+      // XV consecutive cells per thread (vector loads and stores); in the
+      // adjoint instances (ADJ) the adjoint modes 3-5 through cell_adjV
       constexpr int Q = HALF / XV;
       for (int i = threadIdx.x; i < TY * Q; i += blockDim.x) {
         const int r = i / Q, x0 = (i % Q) * XV;
@@ -1339,7 +1497,12 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
           bd[2 * h + 1] = make_float3(ph.c_d * p0.y, ph.c_d * p1.y, ph.c_d * p2.y);
         }
         float km = 0.f;
-        cell_updateV<XV, PC>(a, ph, d, x0, y, z, bd, nm, a.maxdmdt ? &km : nullptr);
+        if constexpr (ADJ) {
+          if (a.mode >= 3) cell_adjV<XV, PC>(a, ph, d, x0, y, z, bd, nm);
+          else cell_updateV<XV, PC>(a, ph, d, x0, y, z, bd, nm, a.maxdmdt ? &km : nullptr);
+        } else {
+          cell_updateV<XV, PC>(a, ph, d, x0, y, z, bd, nm, a.maxdmdt ? &km : nullptr);
+        }
         kmax = fmaxf(kmax, km);
         if (fwd) {
 #pragma unroll
@@ -1469,7 +1632,7 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
 // program's drive slot (a.drive, device memory) instead of the kernel parameters
 // (a separate instantiation, so the constant-field kernel keeps them as
 // constant-bank operands).
-template <int HALF, bool DRIVE, int TYV, bool TMA>
+template <int HALF, bool DRIVE, int TYV, bool TMA, bool ADJ = false>
 // At most 384 threads (3 TY / 2 teams of 32 lanes for 8-row tiles); two CTAs
 // per SM up to px = 512 (the long rows beyond need the registers)
 __global__ void __launch_bounds__(384, HALF >= 512 ? 1 : 2) k_x(StageArgs a, Phys ph, float2* __restrict__ S,
@@ -1482,7 +1645,7 @@ __global__ void __launch_bounds__(384, HALF >= 512 ? 1 : 2) k_x(StageArgs a, Phy
     ph.bx = a.drive[0]; ph.by = a.drive[1]; ph.bz = a.drive[2];
     ph.g1 = a.drive[3]; ph.g2 = a.drive[4];
   }
-  body_x<HALF, TYV, TMA>(a, ph, S, twP, d, TY, fwd, blockIdx.y, blockIdx.x * TY, &xmap);
+  body_x<HALF, TYV, TMA, false, ADJ>(a, ph, S, twP, d, TY, fwd, blockIdx.y, blockIdx.x * TY, &xmap);
 }
 
 // ---------------------------------------------------------------------------
@@ -1601,7 +1764,7 @@ static cudaError_t run_x_ty(const Dims& d, const Phys& ph, const StageArgs& a, c
   threads = (threads + 31) / 32 * 32;
   if (threads < 128) threads = 128;
   if (threads > 512) threads = 512;
-  static bool attr = false, attr_d = false;
+  static bool attr = false, attr_d = false, attr_a = false;
   dim3 grid((d.ny + TY - 1) / TY, d.nz, 1);
   const size_t sm = x_smem(HALF, HALF == 0 ? 0 : TY, TMA);
   alignas(64) CUtensorMap map;
@@ -1611,6 +1774,11 @@ static cudaError_t run_x_ty(const Dims& d, const Phys& ph, const StageArgs& a, c
   if (a.drive) {
     if (cudaError_t e = allow_max_smem(k_x<HALF, true, TYV, TMA>, attr_d)) return e;
     return launch_pdl(d, k_x<HALF, true, TYV, TMA>, grid, dim3(threads), sm, s, a, ph, S, twP, d, TY, fwd, map);
+  }
+  if (a.mode >= 3) {   // the adjoint sweep: its own instance, so the others keep their registers
+    if (cudaError_t e = allow_max_smem(k_x<HALF, false, TYV, TMA, true>, attr_a)) return e;
+    return launch_pdl(d, k_x<HALF, false, TYV, TMA, true>, grid, dim3(threads), sm, s, a, ph, S, twP, d, TY, fwd,
+                      map);
   }
   if (cudaError_t e = allow_max_smem(k_x<HALF, false, TYV, TMA>, attr)) return e;
   return launch_pdl(d, k_x<HALF, false, TYV, TMA>, grid, dim3(threads), sm, s, a, ph, S, twP, d, TY, fwd, map);
