@@ -1634,8 +1634,9 @@ __device__ __forceinline__ void body_x(const StageArgs& a, const Phys& ph, float
 // constant-bank operands).
 template <int HALF, bool DRIVE, int TYV, bool TMA, bool ADJ = false>
 // At most 384 threads (3 TY / 2 teams of 32 lanes for 8-row tiles); two CTAs
-// per SM up to px = 512 (the long rows beyond need the registers)
-__global__ void __launch_bounds__(384, HALF >= 512 ? 1 : 2) k_x(StageArgs a, Phys ph, float2* __restrict__ S,
+// per SM up to px = 512 (the long rows beyond need the registers, and so does
+// the adjoint sweep's two-cell epilogue)
+__global__ void __launch_bounds__(384, (HALF >= 512 || ADJ) ? 1 : 2) k_x(StageArgs a, Phys ph, float2* __restrict__ S,
                                            const float2* __restrict__ twP, Dims d, int TY, int fwd,
                                            const __grid_constant__ CUtensorMap xmap) {
   MM_BC_ENTER(d.flag);
