@@ -270,7 +270,7 @@ int persist_supported(const Dims& d);
 // x tiles of a film in the persistent kernel
 int persist_x_tiles(const Dims& d);
 // kx columns per y/z item and row tiles per x item of the persistent kernel
-static constexpr int kPersistGYZ = 16, kPersistGX = 8;
+static constexpr int kPersistGYZ = 16, kPersistGX = 2;
 // launch it (grid: every SM's resident CTAs); returns 1 or < 0
 int launch_persist(const PersistPlan& p, cudaStream_t s);
 
